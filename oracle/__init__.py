@@ -1,0 +1,223 @@
+"""FP64 CPU oracle for GAME fitness evaluation and GA operators.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` import this package. It shares no code with
+the CUDA path (``paper_1211_5481_gb300``) and neither imports the other.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over
+chromosomes); this module only compiles it and marshals numpy arrays.
+Citations are to Cavuoti et al., arXiv:1211.5481 (Section 3, Eq. 1-6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CHEB, TRIG = 0, 1
+ERR_MSE, ERR_RMSE, ERR_MAE = 0, 1, 2
+
+
+class GAParams(ctypes.Structure):
+    _fields_ = [
+        ("elitism", ctypes.c_int32),
+        ("tournament", ctypes.c_int32),
+        ("thr_pc", ctypes.c_uint32),
+        ("thr_pm", ctypes.c_uint32),
+        ("sigma", ctypes.c_float),
+        ("immigrants", ctypes.c_int32),
+    ]
+
+
+def ga_params(elitism=2, tournament=3, pc=0.9, pm=0.02, sigma=0.1, immigrants=0):
+    """Operator parameters; the rates become 24-bit integer thresholds
+    floor(rate * 2^24), computed once in FP64."""
+    return GAParams(elitism, tournament, int(np.floor(pc * 2.0**24)),
+                    int(np.floor(pm * 2.0**24)), float(np.float32(sigma)), immigrants)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (gcc, -O2, OpenMP, no FP
+    contraction so that FP32 gene updates round once per operation)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        d, i32, i64, u32, u64 = (ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
+                                 ctypes.c_uint32, ctypes.c_uint64)
+        vp = ctypes.c_void_p
+        lib.oracle_num_chromosomes.restype = i64
+        lib.oracle_num_chromosomes.argtypes = [i32, i32]
+        lib.oracle_num_genes_tied.restype = i64
+        lib.oracle_num_genes_tied.argtypes = [i32, i32]
+        lib.oracle_num_genes.restype = i64
+        lib.oracle_num_genes.argtypes = [i32, i32, i32]
+        lib.oracle_basis.argtypes = [i32, i32, d, vp]
+        lib.oracle_output.restype = d
+        lib.oracle_output.argtypes = [vp, vp, i32, i32, i32]
+        lib.oracle_fitness.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp]
+        lib.oracle_fitness_err.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, i32, vp]
+        lib.oracle_fitness_tied.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp]
+        lib.oracle_gram.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
+        lib.oracle_fitness_gram.argtypes = [vp, vp, d, i64, i32, vp, i32, vp]
+        lib.oracle_philox4x32_10.restype = None
+        lib.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+        lib.oracle_init_population.argtypes = [u64, i32, i32, vp]
+        lib.oracle_generation.argtypes = [vp, vp, i32, i32, ctypes.POINTER(GAParams),
+                                          u64, u32, vp]
+        lib.oracle_train.argtypes = [vp, vp, i64, i32, i32, i32, i32,
+                                     ctypes.POINTER(GAParams), u64, i32, i32, vp, vp, vp]
+        lib.oracle_set_threads.argtypes = [i32]
+        _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"{what}: oracle returned {rc}")
+
+
+def set_threads(n: int = 0) -> int:
+    return _load().oracle_set_threads(n)
+
+
+def num_genes(N, d, basis):
+    return int(_load().oracle_num_genes(N, d, basis))
+
+
+def num_genes_tied(d, basis):
+    return int(_load().oracle_num_genes_tied(d, basis))
+
+
+def num_chromosomes(N, basis):
+    return int(_load().oracle_num_chromosomes(N, basis))
+
+
+def basis_values(basis, d, x):
+    """Eq. 1 / Eq. 6: the B*d basis values of the scalar x."""
+    B = 2 if basis == TRIG else 1
+    out = np.zeros(B * d, dtype=np.float64)
+    _check(_load().oracle_basis(basis, d, float(x), _ptr(out)), "basis")
+    return out
+
+
+def output(a, x, d, basis):
+    """Eq. 2 for one chromosome a[K] and one pattern x[N]."""
+    a, x = _f64(a), _f64(x)
+    return float(_load().oracle_output(_ptr(a), _ptr(x), x.shape[0], d, basis))
+
+
+def fitness(X, y, pop, d, basis, err=ERR_MSE):
+    """Eq. 3 averaged over the M patterns (MSE), one value per chromosome."""
+    X, y, pop = _f64(X), _f64(y), _f64(np.atleast_2d(pop))
+    M, N = X.shape
+    P = pop.shape[0]
+    assert pop.shape[1] == num_genes(N, d, basis), "chromosome length"
+    fit = np.zeros(P, dtype=np.float64)
+    _check(_load().oracle_fitness_err(_ptr(X), _ptr(y), M, N, d, basis, _ptr(pop), P,
+                                      err, _ptr(fit)), "fitness")
+    return fit
+
+
+def fitness_tied(X, y, pop, d, basis):
+    X, y, pop = _f64(X), _f64(y), _f64(np.atleast_2d(pop))
+    M, N = X.shape
+    fit = np.zeros(pop.shape[0], dtype=np.float64)
+    assert pop.shape[1] == num_genes_tied(d, basis)
+    _check(_load().oracle_fitness_tied(_ptr(X), _ptr(y), M, N, d, basis, _ptr(pop),
+                                       pop.shape[0], _ptr(fit)), "fitness_tied")
+    return fit
+
+
+def gram(X, y, d, basis):
+    X, y = _f64(X), _f64(y)
+    M, N = X.shape
+    K = num_genes(N, d, basis)
+    G = np.zeros((K, K), dtype=np.float64)
+    b = np.zeros(K, dtype=np.float64)
+    yy = np.zeros(1, dtype=np.float64)
+    _check(_load().oracle_gram(_ptr(X), _ptr(y), M, N, d, basis, _ptr(G), _ptr(b),
+                               _ptr(yy)), "gram")
+    return G, b, float(yy[0]), M
+
+
+def fitness_gram(gram_state, pop):
+    G, b, yy, M = gram_state
+    pop = _f64(np.atleast_2d(pop))
+    fit = np.zeros(pop.shape[0], dtype=np.float64)
+    _check(_load().oracle_fitness_gram(_ptr(G), _ptr(b), yy, M, G.shape[0], _ptr(pop),
+                                       pop.shape[0], _ptr(fit)), "fitness_gram")
+    return fit
+
+
+def philox4x32_10(key, ctr):
+    """Philox4x32-10 of counters ctr[n][4] under the 64-bit key."""
+    ctr = np.ascontiguousarray(np.atleast_2d(ctr), dtype=np.uint32)
+    k = np.array([key & 0xFFFFFFFF, (key >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    out = np.zeros_like(ctr)
+    lib = _load()
+    for n in range(ctr.shape[0]):
+        lib.oracle_philox4x32_10(_ptr(k), _ptr(ctr[n]), _ptr(out[n]))
+    return out
+
+
+def init_population(seed, P, K):
+    pop = np.zeros((P, K), dtype=np.float32)
+    _check(_load().oracle_init_population(seed, P, K, _ptr(pop)), "init_population")
+    return pop
+
+
+def generation(pop, fit, seed, g, prm=None):
+    prm = prm or ga_params()
+    pop = np.ascontiguousarray(pop, dtype=np.float32)
+    fit = _f64(fit)
+    P, K = pop.shape
+    nxt = np.zeros_like(pop)
+    _check(_load().oracle_generation(_ptr(pop), _ptr(fit), P, K, ctypes.byref(prm),
+                                     seed, g, _ptr(nxt)), "generation")
+    return nxt
+
+
+def train(X, y, d, basis, P, G, seed, prm=None, use_gram=False):
+    """Whole GA run; returns (pop[P][K] float32, fit[P], best[G+1])."""
+    prm = prm or ga_params()
+    X, y = _f64(X), _f64(y)
+    M, N = X.shape
+    K = num_genes(N, d, basis)
+    pop = np.zeros((P, K), dtype=np.float32)
+    fit = np.zeros(P, dtype=np.float64)
+    best = np.zeros(G + 1, dtype=np.float64)
+    _check(_load().oracle_train(_ptr(X), _ptr(y), M, N, d, basis, P, ctypes.byref(prm),
+                                seed, G, int(use_gram), _ptr(pop), _ptr(fit),
+                                _ptr(best)), "train")
+    return pop, fit, best

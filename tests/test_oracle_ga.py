@@ -1,0 +1,249 @@
+"""Pins of the oracle's GA operators by invariants the definitions fix:
+constant population size, verbatim elites, crossover that only exchanges
+genes inside a parent pair, genes kept in [-1, 1], elitist best fitness that
+never worsens, exact resume, and the rates of the random decisions."""
+import numpy as np
+import pytest
+
+from paper_1211_5481_gb300 import datagen as dg
+
+CHEB = 0
+
+
+def _fit_key(f):
+    return np.where(np.isnan(f), np.inf, f)
+
+
+def _elites(fit, E):
+    order = np.lexsort((np.arange(fit.size), _fit_key(fit)))
+    return order[:E]
+
+
+def test_init_population_range_and_uniformity(orc):
+    pop = orc.init_population(42, 256, 33)
+    assert pop.dtype == np.float32 and pop.shape == (256, 33)
+    assert pop.min() >= -1.0 and pop.max() < 1.0
+    # U[-1,1): mean 0, variance 1/3
+    assert abs(pop.mean()) < 0.01 and abs(pop.var() - 1 / 3) < 0.01
+    # genes are multiples of 2^-23
+    assert np.all(pop * 2.0**23 == np.round(pop * 2.0**23))
+    # different seeds give different populations, same seed the same one
+    assert not np.array_equal(pop, orc.init_population(43, 256, 33))
+    assert np.array_equal(pop, orc.init_population(42, 256, 33))
+
+
+@pytest.mark.parametrize("P,E", [(64, 2), (65, 2), (10, 0), (9, 3)])
+def test_generation_invariants(orc, P, E):
+    K = 17
+    rng = np.random.default_rng(P + E)
+    pop = orc.init_population(7, P, K)
+    fit = rng.uniform(0, 1, P)
+    fit[3] = fit[5]  # a tie, broken by the lower index
+    prm = orc.ga_params(elitism=E, pm=0.0)   # no mutation: pure crossover
+    nxt = orc.generation(pop, fit, 77, 3, prm)
+    assert nxt.shape == pop.shape
+    # elites verbatim, in rank order
+    for e, src in enumerate(_elites(fit, E)):
+        np.testing.assert_array_equal(nxt[e], pop[src])
+    # every child gene comes from a population member at the same locus, and
+    # each pair's two children hold, per locus, the genes of two parents
+    for s in range(E, P):
+        for k in range(K):
+            assert nxt[s, k] in pop[:, k]
+    for q in range((P - E) // 2):
+        a, b = nxt[E + 2 * q], nxt[E + 2 * q + 1]
+        # find the parents: members whose genes match at locus 0 and K-1
+        pa = [p for p in range(P) if pop[p, 0] == a[0]]
+        pb = [p for p in range(P) if pop[p, 0] == b[0]]
+        ok = False
+        for i in pa:
+            for j in pb:
+                if all(sorted((a[k], b[k])) == sorted((pop[i, k], pop[j, k]))
+                       for k in range(K)):
+                    ok = True
+        assert ok, f"pair {q} is not a crossover of two members"
+    assert np.all(np.abs(nxt) <= 1.0)
+
+
+def _tagged_population(P, K):
+    """Member p holds gene (p*K + k) * 2^-20 at locus k, so the source member
+    and locus of any copied gene can be read back exactly."""
+    assert P * K < 2**20
+    return ((np.arange(P)[:, None] * K + np.arange(K)[None, :]) * 2.0**-20).astype(np.float32)
+
+
+def _source(pop_tagged, v, K):
+    idx = np.round(np.asarray(v, dtype=np.float64) * 2.0**20).astype(np.int64)
+    return idx // K, idx % K
+
+
+def test_crossover_is_one_point(orc):
+    """Each child is a head of one parent joined to the tail of the other at a
+    single cut in [1, K-1] (or an unchanged copy); genes keep their locus."""
+    P, K = 40, 25
+    pop = _tagged_population(P, K)
+    fit = np.linspace(1, 2, P)
+    nxt = orc.generation(pop, fit, 5, 0, orc.ga_params(elitism=2, pm=0.0))
+    for s in range(2, P):
+        member, locus = _source(pop, nxt[s], K)
+        np.testing.assert_array_equal(locus, np.arange(K))
+        assert np.count_nonzero(np.diff(member)) <= 1
+    for q in range((P - 2) // 2):
+        ma, _ = _source(pop, nxt[2 + 2 * q], K)
+        mb, _ = _source(pop, nxt[3 + 2 * q], K)
+        # the two children hold complementary parents at every locus
+        for k in range(K):
+            assert sorted((ma[k], mb[k])) == sorted((ma[0], mb[0]))
+        cut_a = np.nonzero(np.diff(ma))[0]
+        cut_b = np.nonzero(np.diff(mb))[0]
+        np.testing.assert_array_equal(cut_a, cut_b)
+
+
+def test_rates(orc):
+    """Crossover happens for ~pc of the pairs, mutation for ~pm of the
+    genes, and the Irwin-Hall steps have mean 0 and sd sigma."""
+    P, K = 402, 65
+    pop = _tagged_population(P, K)
+    fit = np.arange(P, dtype=np.float64)
+    pc = 0.6
+    crossed = pairs = same = 0
+    for g in range(10):
+        nxt = orc.generation(pop, fit, 11, g, orc.ga_params(elitism=2, pc=pc, pm=0.0))
+        for q in range((P - 2) // 2):
+            ma, _ = _source(pop, nxt[2 + 2 * q], K)
+            mb, _ = _source(pop, nxt[3 + 2 * q], K)
+            same += ma[0] == mb[0]
+            crossed += ma[0] != ma[-1]
+            pairs += 1
+    # a crossed pair of identical parents looks uncrossed; count those out
+    assert abs(crossed / (pairs - same) - pc) < 0.04
+    pm, sigma = 0.05, 0.01
+    zero = np.zeros((P, K), dtype=np.float32)   # children = sigma * z exactly
+    steps = []
+    for g in range(4):
+        nxt = orc.generation(zero, fit, 13, g, orc.ga_params(elitism=2, pc=0.9, pm=pm,
+                                                            sigma=sigma))
+        assert np.all(nxt[:2] == 0)
+        steps.append(nxt[2:].reshape(-1))
+    steps = np.concatenate(steps).astype(np.float64)
+    mutated = steps[steps != 0]
+    assert abs(mutated.size / steps.size - pm) < 0.004
+    assert abs(mutated.mean()) < 0.05 * sigma
+    assert abs(mutated.std() / sigma - 1) < 0.05
+    # Irwin-Hall-12 is bounded by 6 sd
+    assert np.abs(mutated).max() <= 6 * sigma * (1 + 1e-6)
+
+
+def test_tournament_prefers_fitter(orc):
+    """With tournaments of 3 the chance of selecting the best-ranked member
+    is 1 - (1 - 1/P)^3 per draw; the top decile dominates the parents."""
+    P, K = 200, 9
+    pop = np.zeros((P, K), dtype=np.float32)
+    pop[:, 0] = np.arange(P) / 256.0       # identifies the member
+    fit = np.arange(P, dtype=np.float64)   # member p has rank p
+    prm = orc.ga_params(elitism=0, pc=0.0, pm=0.0)
+    ranks = []
+    for g in range(20):
+        nxt = orc.generation(pop, fit, 21, g, prm)
+        ranks.extend((nxt[:, 0] * 256).round().astype(int).tolist())
+    ranks = np.array(ranks)
+    # P(rank < P/10) for the min of 3 uniform draws = 1 - 0.9^3 = 0.271
+    assert abs(np.mean(ranks < P // 10) - 0.271) < 0.03
+    # the worst member can only win when drawn three times
+    assert np.mean(ranks == P - 1) < 0.001
+
+
+def test_nan_fitness_never_elite(orc):
+    P, K = 12, 5
+    pop = orc.init_population(1, P, K)
+    fit = np.linspace(0.1, 1.0, P)
+    fit[0] = np.nan
+    nxt = orc.generation(pop, fit, 2, 0, orc.ga_params(elitism=2))
+    np.testing.assert_array_equal(nxt[0], pop[1])
+    np.testing.assert_array_equal(nxt[1], pop[2])
+
+
+def test_immigrants_fill_last_slots(orc):
+    P, K, I = 20, 7, 3
+    pop = orc.init_population(1, P, K)
+    fit = np.linspace(0.1, 1.0, P)
+    nxt = orc.generation(pop, fit, 4, 2, orc.ga_params(elitism=2, immigrants=I))
+    fresh = nxt[P - I:]
+    assert np.all(fresh >= -1) and np.all(fresh < 1)
+    assert np.all(fresh * 2.0**23 == np.round(fresh * 2.0**23))
+    assert not np.any([np.any(np.all(pop == r, axis=1)) for r in fresh])
+
+
+def test_generation_rejects_bad_params(orc):
+    pop = orc.init_population(1, 4, 5)
+    with pytest.raises(ValueError):
+        orc.generation(pop, np.zeros(4), 1, 0, orc.ga_params(elitism=3))
+    with pytest.raises(ValueError):
+        orc.generation(pop, np.zeros(4), 1, 0, orc.ga_params(tournament=0))
+
+
+def test_train_elitist_best_never_worsens(orc):
+    pr = dg.regression(21, 400, 4, 3, 0.05, degree=3)
+    _, fit, best = orc.train(pr.X, pr.y, 3, CHEB, 24, 30, seed=5)
+    assert np.all(np.diff(best) <= 0.0)
+    assert best[-1] < best[0]
+    assert best[-1] == fit.min()
+
+
+def test_train_resume_is_exact(orc):
+    """Counter-based draws depend only on (seed, g, slot, gene): running
+    G1 generations, then continuing from that state, equals one run of
+    G1 + G2 generations."""
+    pr = dg.regression(22, 300, 3, 2, 0.05, degree=2)
+    prm = orc.ga_params()
+    pop_full, fit_full, _ = orc.train(pr.X, pr.y, 2, CHEB, 16, 12, seed=8, prm=prm)
+    pop, fit, _ = orc.train(pr.X, pr.y, 2, CHEB, 16, 5, seed=8, prm=prm)
+    for g in range(5, 12):
+        pop = orc.generation(pop, fit, 8, g, prm)
+        fit = orc.fitness(pr.X, pr.y, pop, 2, CHEB)
+    np.testing.assert_array_equal(pop, pop_full)
+    np.testing.assert_array_equal(fit, fit_full)
+
+
+def test_train_gram_matches_direct(orc):
+    pr = dg.regression(23, 300, 3, 2, 0.05, degree=2)
+    pd_, fd, bd = orc.train(pr.X, pr.y, 2, CHEB, 16, 6, seed=9)
+    pg, fg, bg = orc.train(pr.X, pr.y, 2, CHEB, 16, 6, seed=9, use_gram=True)
+    np.testing.assert_allclose(bg, bd, rtol=1e-9)
+
+
+def test_cut_points_uniform(orc):
+    """The cut is uniform over [1, K-1]: with K = 5 each head length 1..4
+    occurs for about a quarter of the crossed pairs."""
+    P, K = 402, 5
+    pop = _tagged_population(P, K)
+    fit = np.arange(P, dtype=np.float64)
+    heads = []
+    for g in range(6):
+        nxt = orc.generation(pop, fit, 17, g, orc.ga_params(elitism=2, pc=1.0, pm=0.0))
+        for q in range((P - 2) // 2):
+            ma, _ = _source(pop, nxt[2 + 2 * q], K)
+            mb, _ = _source(pop, nxt[3 + 2 * q], K)
+            if ma[0] == mb[0]:
+                continue   # identical parents: the cut is invisible
+            heads.append(int(np.count_nonzero(ma == ma[0])))
+    counts = np.bincount(heads, minlength=K + 1)
+    assert counts[0] == 0 and counts[K] == 0
+    frac = counts[1:K] / len(heads)
+    assert np.all(np.abs(frac - 0.25) < 0.04)
+
+
+def test_mutation_clamps_both_ends(orc):
+    """Genes at the bounds pushed by large steps stay in [-1, 1] and land
+    exactly on the bound when the step overshoots."""
+    P, K = 64, 33
+    pop = np.ones((P, K), dtype=np.float32)
+    pop[P // 2:] = -1.0
+    fit = np.arange(P, dtype=np.float64)
+    nxt = orc.generation(pop, fit, 3, 0, orc.ga_params(elitism=2, pc=0.0, pm=1.0, sigma=0.5))
+    assert nxt.min() >= -1.0 and nxt.max() <= 1.0
+    child = nxt[2:]
+    # half the steps overshoot: many genes sit exactly on a bound, the rest
+    # moved inwards
+    assert np.count_nonzero(np.abs(child) == 1.0) > 0.3 * child.size
+    assert np.count_nonzero(np.abs(child) < 1.0) > 0.3 * child.size

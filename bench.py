@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the GAME generation step on one GB300 (or N independent
+replicas under torchrun), printing one JSON line.
+
+Workload (default): the large classification set, M = 1,000,000 patterns,
+N = 32 correlated features scaled to [-1, 1], Chebyshev degree 8 (K = 257
+genes), P = 1024 chromosomes, sign targets with 5% flips; seeded synthetic
+data generated on the host and uploaded before timing. One step is one
+generation: selection / crossover / mutation kernels, the population pack,
+the fused fitness contraction (tensor cores, BF16 operands, FP32
+accumulation) and the FP64 cross-tile error sum. The plain FP32 CUDA-core
+form of the same step is timed beside it, and a sample of chromosomes is
+re-scored by the FP64 oracle to state the accuracy of both.
+
+Metric: chromosome-pattern fitness evaluations per second (M * P / step
+time), whole job (sum over ranks / max time). `--impl reference` times the
+FP64 CPU oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("chromosome-pattern fitness evals/s and generations/s vs plain FP32 GPU "
+          "at stated accuracy")
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--M", type=int, default=1_000_000, help="patterns (smaller for profiling)")
+    ap.add_argument("--form", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--no-fp32-leg", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.proc = None
+        self.index = index
+        if enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError:
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample_rate(pr, P_s, target_s=8.0, max_s=25.0):
+    """FP64 oracle (direct form, all host cores) evals/s on a bounded sample:
+    the first M_s patterns x P_s chromosomes, M_s doubled until one call takes
+    target_s seconds."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    pop = oracle.init_population(2, P_s, pr.K)
+    M_s = 2000
+    while True:
+        t0 = time.perf_counter()
+        oracle.fitness(pr.X[:M_s], pr.y[:M_s], pop, pr.degree, pr.basis)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or M_s >= pr.M or dt * 2 > max_s:
+            break
+        M_s = min(pr.M, M_s * 2 if dt < target_s / 4 else int(M_s * target_s / max(dt, 1e-3)))
+    return {"value": M_s * P_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {M_s} patterns x {P_s} chromosomes of the workload, "
+                      f"direct-form FP64 fitness, {dt:.2f} s"}, M_s
+
+
+def workload(M):
+    from paper_1211_5481_gb300 import datagen as dg
+    pr = dg.large_classification(M=M)
+    return pr
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pr = workload(args.M)
+    P = pr.P
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(0)
+    # size one step to a few seconds of CPU work
+    _, M_s = oracle_sample_rate(pr, 16, target_s=2.0, max_s=6.0)
+    pop = oracle.init_population(2, 16, pr.K)
+    for _ in range(args.warmup):
+        oracle.fitness(pr.X[:M_s], pr.y[:M_s], pop, pr.degree, pr.basis)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fitness(pr.X[:M_s], pr.y[:M_s], pop, pr.degree, pr.basis)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = M_s * 16 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": pr.name, "M": pr.M, "N": pr.N, "degree": pr.degree,
+                       "K": pr.K, "P": P, "basis": "chebyshev",
+                       "step": f"oracle direct-form fitness of 16 chromosomes over the first "
+                               f"{M_s} patterns"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {M_s} patterns x 16 chromosomes per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_1211_5481_gb300 import game
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    pr = workload(args.M)
+    M, K, P = pr.M, pr.K, pr.P
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    game.load()
+    prec = game.GAME_PREC_BF16 if args.form == "bf16" else game.GAME_PREC_FP32
+    g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(handle, steps, warmup):
+        for _ in range(warmup):
+            game.game_generation(handle.h, 2)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        handle.set_timing(True)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()   # L2 flush between steps, outside the timed events
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            game.game_generation(handle.h, 2)
+            b.record(stream)
+            ms.append((a, b))
+        torch.cuda.synchronize(dev)
+        tm = handle.timing()
+        handle.set_timing(False)
+        step_ms = [x.elapsed_time(y) for x, y in ms]
+        if world > 1:
+            dist.barrier()
+        return step_ms, tm
+
+    # main leg
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    step_ms, tm = timed_steps(g, args.steps, max(args.warmup, 3))
+    clk = clocks.stop()
+    t_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = M * P * world / (t_step * 1e-3)
+
+    peaks, peak_src = load_peaks()
+    flops_launch = 2.0 * M * P * (K - 1) + 3.0 * M * P
+    fit_ms = tm["fitness_ms"] / max(tm["fitness_launches"], 1)
+    achieved_tflops = flops_launch / (fit_ms * 1e-3) / 1e12
+    if prec == game.GAME_PREC_BF16:
+        peak = float(peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops (burst)",
+                "frac_of_sustained": achieved_tflops / float(peaks.get("bf16_tflops_sustained",
+                                                                        peak)),
+                "kernel": "fitness_tc_kernel", "kernel_ms": fit_ms}
+    else:
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * 128 * 2 * float(peaks["sm_max_mhz"]) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak, "traffic": None,
+                "peak_source": "FP32 FFMA: SMs x 128 lanes x 2 flop x max SM clock",
+                "kernel": "fitness_fp32_kernel", "kernel_ms": fit_ms}
+
+    # plain FP32 GPU form of the same step, for the "vs plain FP32" ratio
+    fp32_leg = None
+    if prec == game.GAME_PREC_BF16 and not args.no_fp32_leg:
+        g32 = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P,
+                        precision=game.GAME_PREC_FP32, seed=2)
+        ms32, tm32 = timed_steps(g32, max(3, args.steps // 4), 3)
+        t32 = sum(ms32) / len(ms32)
+        fp32_leg = {"value": M * P * world / (t32 * 1e-3), "ms_per_step": t32,
+                    "fitness_kernel_ms": tm32["fitness_ms"] / max(tm32["fitness_launches"], 1)}
+        g32.close()
+
+    # end to end through the public API: a host population (pinned) in, its
+    # fitness out, one synchronous call per step
+    pin_pop = torch.empty((P, K), dtype=torch.float32).pin_memory()
+    pop_np, _, _ = g.population()
+    pin_pop.copy_(torch.from_numpy(pop_np))
+    pin_fit = torch.empty(P, dtype=torch.float64).pin_memory()
+    popv, fitv = pin_pop.numpy(), pin_fit.numpy()
+    for _ in range(2):
+        g.eval_fitness(popv)
+        game.game_eval_fitness(g.h, popv, fitv)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        game.game_eval_fitness(g.h, popv, fitv)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+    e2e = {"value": M * P * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": P * K * 4,
+           "d2h_bytes_per_step": P * 8,
+           "call": "game_eval_fitness(host pinned pop[P][K]) -> host fit[P]"}
+
+    # accuracy of the timed forms on a sample of the current population
+    acc = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pop_np, fit_np, gen = g.population()
+        sample = np.linspace(0, P - 1, 8).astype(int)
+        ref = oracle.fitness(pr.X, pr.y, pop_np[sample], pr.degree, pr.basis)
+        f_bf = g.eval_fitness(pop_np, precision=game.GAME_PREC_BF16)
+        f_32 = g.eval_fitness(pop_np, precision=game.GAME_PREC_FP32)
+        acc = {"sample_chromosomes": len(sample), "generation": gen,
+               "bf16_max_rel_err": float(np.max(np.abs(f_bf[sample] - ref) / ref)),
+               "fp32_max_rel_err": float(np.max(np.abs(f_32[sample] - ref) / ref)),
+               "top10_agreement_bf16_vs_fp32": len(set(np.argsort(f_bf)[:10]) &
+                                                    set(np.argsort(f_32)[:10])) / 10}
+        cpu, _ = oracle_sample_rate(pr, 16)
+
+    n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
+        2 * tm["operators_launches"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec else "f32",
+        "data": "synthetic",
+        "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
+                   "basis": "chebyshev", "contraction": args.form,
+                   "step": "one generation: operators + pack + fused fitness + FP64 reduce",
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "generations_per_s": 1e3 / t_step,
+        "vs_fp32": (value / fp32_leg["value"]) if fp32_leg else None,
+        "fp32_form": fp32_leg,
+        "stage_ms_per_step": {k.replace("_ms", ""): tm[k] / max(args.steps, 1)
+                              for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms")},
+        "accuracy": acc,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(n_launch),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

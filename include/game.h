@@ -1,0 +1,166 @@
+/*
+ * game.h -- C ABI of libgame.so: GAME population fitness evaluation and
+ * genetic operators on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Cavuoti, Garofalo, Brescia, Pescape, Longo, Ventre, "Genetic
+ * Algorithm Modeling with GPU Parallel Computing Technology",
+ * arXiv:1211.5481. Section numbers and equations below are that paper's.
+ *
+ * Notation: M patterns (the paper's NP), N features per pattern, d degree,
+ * B = 1 (Chebyshev basis T_j) or 2 (trigonometric basis cos(jx), sin(jx),
+ * the paper's "polytrigo", Eq. 6), K = B*N*d + 1 genes per chromosome,
+ * P chromosomes. Chromosome p is a row pop[p][0..K-1] of FP32 genes:
+ * gene 0 is the bias a_0 and gene 1 + i*B*d + b*d + (j-1) weights
+ * phi_{b,j}(x_i) (b = 0: T_j or cos(j x); b = 1: sin(j x)).
+ *
+ * Fitness is the mean squared error of Eq. 3 over all M patterns
+ * (Section 3; Section 5 sets MSE as the error function), lower is better.
+ *
+ * Conventions for every call:
+ *  - Returns GAME_OK (0) or a negative GAME_E* code; game_last_error()
+ *    then describes the failure (thread-local string, valid until the
+ *    calling thread's next call).
+ *  - Pointers are "host or device": the library asks the CUDA driver which
+ *    kind each pointer is. Device pointers must be on the handle's device.
+ *  - All GPU work goes on the stream given to game_create. Calls with host
+ *    output pointers synchronise that stream before returning; calls whose
+ *    outputs are device pointers only enqueue work (use game_sync).
+ *  - A handle is not thread-safe; distinct handles are independent.
+ *  - Arrays are row-major and owned by the caller; the handle owns its own
+ *    device copies.
+ */
+#ifndef GAME_H
+#define GAME_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAME_OK 0
+#define GAME_EINVAL (-1)   /* bad argument, shape, value or non-finite data */
+#define GAME_ENOMEM (-2)   /* host or device allocation failed */
+#define GAME_ECUDA (-3)    /* CUDA runtime error (message has the details) */
+#define GAME_ETIMEOUT (-4) /* a kernel's bounded wait ran out; results void */
+#define GAME_ESTATE (-5)   /* call not valid in the handle's current state */
+
+#define GAME_BASIS_CHEB 0
+#define GAME_BASIS_TRIG 1
+
+/* Arithmetic of the fitness contraction (the expansion-times-genes sum). */
+#define GAME_PREC_FP32 0   /* FP32 CUDA-core FFMA, FP32 accumulation */
+#define GAME_PREC_BF16 1   /* tcgen05 BF16 x BF16 -> FP32 in tensor memory */
+
+typedef struct game_ctx* game_t;
+
+/* GA and evaluation settings. Section 5 lists the paper's own settings:
+ * crossover rate 0.9, mutation rate 0.2, 2 elites, MSE stop threshold
+ * 0.001, roulette/ranking selection. The defaults here keep crossover 0.9
+ * and 2 elites, use tournaments of 3, per-gene mutation rate 0.02 with
+ * Gaussian steps of sd 0.1, and no stop threshold. */
+typedef struct {
+  int32_t P;            /* chromosomes; 0 = B*N + 1 (Eq. 4) */
+  int32_t elitism;      /* E >= 0 best chromosomes copied unchanged */
+  int32_t tournament;   /* candidates per tournament, 1..64 */
+  int32_t precision;    /* GAME_PREC_* */
+  int32_t immigrants;   /* fresh random chromosomes per generation (Section 4) */
+  int32_t check_every;  /* generations between stop-rule checks in game_train */
+  float pc;             /* crossover probability, [0, 1] */
+  float pm;             /* per-gene mutation probability, [0, 1] */
+  float sigma;          /* sd of the Gaussian mutation step, >= 0 */
+  float reserved_f;
+  double mse_threshold; /* game_train stops once best fitness < this; <= 0 off */
+  uint64_t seed;        /* key of the counter-based generator (Philox4x32-10) */
+  int32_t reserved[8];  /* must be zero */
+} game_params;
+
+/* Fills *out with the defaults listed above. */
+int game_params_default(game_params* out);
+
+/* Creates a handle for one training set and copies it to the device.
+ *   X [M][N] FP32 features, y [M] FP32 targets (host or device memory).
+ *   degree d >= 1; basis GAME_BASIS_CHEB or GAME_BASIS_TRIG.
+ *   prm: settings (NULL = defaults); cuda_stream: a cudaStream_t, or NULL
+ *   for the legacy default stream.
+ * Validation (GAME_EINVAL): M < 1, N < 1, d < 1, unknown basis, NaN/Inf in
+ * X or y, |x| > 1 with the Chebyshev basis, P < E + immigrants + 2,
+ * tournament outside 1..64, rates outside [0, 1], sigma < 0, K > 4097.
+ * The population is initialised with genes uniform in [-1, 1) (Section 3)
+ * from prm->seed and evaluated, so the handle starts at generation 0 with
+ * a valid fitness vector. Synchronous. */
+int game_create(const float* X, const float* y, int64_t M, int32_t N,
+                int32_t degree, int32_t basis, const game_params* prm,
+                void* cuda_stream, game_t* out);
+
+/* Shape queries. */
+int game_get_shape(game_t h, int64_t* M, int32_t* N, int32_t* K, int32_t* P);
+
+/* Fitness of a caller-supplied population (Eq. 2, Eq. 3, MSE):
+ *   pop [P][K] FP32 genes, fit_out [P] FP64, both host or both device.
+ * P >= 1 may differ from the handle's population size. Uses the handle's
+ * precision. Does not touch the handle's GA state. */
+int game_eval_fitness(game_t h, const float* pop, int32_t P, double* fit_out);
+
+/* Like game_eval_fitness with the contraction arithmetic chosen per call
+ * (GAME_PREC_*). */
+int game_eval_fitness_prec(game_t h, const float* pop, int32_t P,
+                           int32_t precision, double* fit_out);
+
+/* One generation g -> g+1 of the GA state: elitism, tournament selection,
+ * one-point crossover, per-gene Gaussian mutation, clamping to [-1, 1]
+ * (Section 3 names the operators; Section 5 the rates), then the fitness of
+ * the new population. All random decisions come from Philox4x32-10 keyed
+ * by `seed` with counters built from (g, slot, gene, purpose), so a run is
+ * reproducible and resumable. Enqueues only. */
+int game_generation(game_t h, uint64_t seed);
+
+/* Runs up to `generations` generations with prm->seed, stopping early once
+ * the best fitness drops below prm->mse_threshold (checked every
+ * check_every generations; Section 4: training stops at the iteration limit
+ * or the error threshold). *generations_run (may be NULL) receives the
+ * count. Synchronous. */
+int game_train(game_t h, int32_t generations, int32_t* generations_run);
+
+/* Copies out the current population [P][K] FP32, its fitness [P] FP64 and
+ * the generation counter; any output may be NULL. Host or device outputs
+ * (pop_out and fit_out in the same kind of memory). */
+int game_get_population(game_t h, float* pop_out, double* fit_out,
+                        int64_t* generation);
+
+/* Replaces the GA state: population [P][K] (the handle's P), its fitness
+ * [P] (NULL = evaluate it now) and the generation counter. Together with
+ * game_get_population this is checkpoint / resume. */
+int game_set_state(game_t h, const float* pop, const double* fit,
+                   int64_t generation);
+
+/* Per-stage device timing (CUDA events recorded on the handle's stream
+ * around each kernel launch of the stages below). */
+typedef struct {
+  double fitness_ms;        /* fused fitness contraction kernel */
+  double pack_ms;           /* population -> contraction operand layout */
+  double reduce_ms;         /* cross-tile FP64 error sum */
+  double operators_ms;      /* selection / crossover / mutation kernels */
+  int64_t fitness_launches;
+  int64_t pack_launches;
+  int64_t reduce_launches;
+  int64_t operators_launches;
+} game_timing;
+
+/* enable != 0 starts recording (and clears the totals); 0 stops. */
+int game_set_timing(game_t h, int32_t enable);
+/* Synchronises the stream and returns the totals since the last enable. */
+int game_get_timing(game_t h, game_timing* out);
+
+/* Waits for the handle's stream and reports a kernel timeout, if any. */
+int game_sync(game_t h);
+
+/* Releases the handle and all its device memory (NULL is accepted). */
+int game_destroy(game_t h);
+
+/* Description of the calling thread's last failure ("" if none). */
+const char* game_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

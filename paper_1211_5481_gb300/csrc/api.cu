@@ -1,0 +1,610 @@
+// api.cu -- the C ABI of libgame.so (declared in include/game.h): handle
+// lifetime, argument validation, memory-space detection, device buffers and
+// the sequencing of the kernels of one evaluation / one generation.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "game_internal.cuh"
+
+using namespace game;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return GAME_ECUDA;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+// Device pointer test: the driver knows every allocation it made.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace
+
+struct game_ctx {
+  Shape s{};
+  game_params prm{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  float* Xt = nullptr;
+  float* y = nullptr;
+  float* pop[2] = {nullptr, nullptr};
+  int cur = 0;
+  double* fit = nullptr;
+  bool fit_valid = false;
+  int64_t gen = 0;
+  int4* plan = nullptr;
+  int* status = nullptr;   // device status word written by kernels
+  // evaluation scratch, grown on demand
+  int cap_P = 0;
+  float* popT = nullptr;
+  uint8_t* popA = nullptr;
+  float* a0 = nullptr;
+  double* part = nullptr;
+  size_t part_cap = 0;
+  float* upop = nullptr;    // device copy of a host population
+  double* ufit = nullptr;
+  int ucap = 0;
+  size_t popT_cap = 0, popA_cap = 0;
+  // per-stage timing
+  bool timing = false;
+  struct Span {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Span> spans;
+  double tot_ms[4] = {0, 0, 0, 0};
+  int64_t count[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+enum StageKind { kFitness = 0, kPack = 1, kReduce = 2, kOperators = 3 };
+
+// Records the start event of a timed stage (no-op when timing is off).
+cudaEvent_t stage_begin(game_ctx* h) {
+  if (!h->timing) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, h->st);
+  return e;
+}
+
+void harvest_spans(game_ctx* h) {
+  for (auto& sp : h->spans) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(sp.b) == cudaSuccess && cudaEventElapsedTime(&ms, sp.a, sp.b) ==
+        cudaSuccess) {
+      h->tot_ms[sp.kind] += ms;
+      h->count[sp.kind] += 1;
+    }
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  h->spans.clear();
+}
+
+void stage_end(game_ctx* h, cudaEvent_t start, int kind) {
+  if (!start) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaEventDestroy(start);
+    return;
+  }
+  cudaEventRecord(e, h->st);
+  h->spans.push_back({start, e, kind});
+  if (h->spans.size() > 8192) harvest_spans(h);
+}
+
+int ensure_scratch(game_ctx* h, int P, int prec) {
+  const int Ppad = ceil_div(P, 128) * 128;
+  if (Ppad > h->cap_P) {
+    dev_free(h->a0);
+    h->a0 = nullptr;
+    if (dev_alloc(&h->a0, Ppad) != cudaSuccess) return fail(GAME_ENOMEM, "a0 allocation");
+    h->cap_P = Ppad;
+  }
+  if (prec == GAME_PREC_FP32) {
+    const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
+    const size_t need = (size_t)pl.Kc * Ppad;
+    if (need > h->popT_cap) {
+      dev_free(h->popT);
+      h->popT = nullptr;
+      if (dev_alloc(&h->popT, need) != cudaSuccess) return fail(GAME_ENOMEM, "popT allocation");
+      h->popT_cap = need;
+    }
+    const size_t pneed = (size_t)pl.grid_y * Ppad;
+    if (pneed > h->part_cap) {
+      dev_free(h->part);
+      h->part = nullptr;
+      if (dev_alloc(&h->part, pneed) != cudaSuccess) return fail(GAME_ENOMEM, "partials");
+      h->part_cap = pneed;
+    }
+  } else {
+    const TcPlan pl = plan_tc(h->s, P, h->num_sms);
+    if (!pl.ok)
+      return fail(GAME_EINVAL, "contraction length too large for the tensor-core path");
+    const size_t need = (size_t)pl.C * pl.KB * 128 * 128;
+    if (need > h->popA_cap) {
+      dev_free(h->popA);
+      h->popA = nullptr;
+      if (dev_alloc(&h->popA, need) != cudaSuccess) return fail(GAME_ENOMEM, "popA allocation");
+      h->popA_cap = need;
+    }
+    const size_t pneed = (size_t)pl.rows * Ppad;
+    if (pneed > h->part_cap) {
+      dev_free(h->part);
+      h->part = nullptr;
+      if (dev_alloc(&h->part, pneed) != cudaSuccess) return fail(GAME_ENOMEM, "partials");
+      h->part_cap = pneed;
+    }
+  }
+  return GAME_OK;
+}
+
+// Enqueues the fitness of a device population dpop [P][K] into dfit [P].
+int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
+  int rc = ensure_scratch(h, P, prec);
+  if (rc) return rc;
+  const int Ppad = ceil_div(P, 128) * 128;
+  cudaEvent_t t0;
+  if (prec == GAME_PREC_FP32) {
+    const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
+    t0 = stage_begin(h);
+    CK(launch_pack_fp32(dpop, P, Ppad, h->s, pl.Kc, h->popT, h->a0, h->st));
+    stage_end(h, t0, kPack);
+    t0 = stage_begin(h);
+    CK(launch_fitness_fp32(pl, h->s, h->Xt, h->y, h->popT, h->a0, P, Ppad, h->part, h->st));
+    stage_end(h, t0, kFitness);
+    t0 = stage_begin(h);
+    CK(launch_reduce(h->part, pl.grid_y, P, Ppad, h->s.M, dfit, h->st));
+    stage_end(h, t0, kReduce);
+  } else {
+    const TcPlan pl = plan_tc(h->s, P, h->num_sms);
+    t0 = stage_begin(h);
+    CK(launch_pack_bf16(dpop, P, pl.C, h->s, pl.KB, h->popA, h->a0, h->st));
+    stage_end(h, t0, kPack);
+    t0 = stage_begin(h);
+    CK(launch_fitness_tc(pl, h->s, h->Xt, h->y, h->popA, h->a0, P, Ppad, h->part, h->status,
+                         h->st));
+    stage_end(h, t0, kFitness);
+    t0 = stage_begin(h);
+    CK(launch_reduce(h->part, pl.rows, P, Ppad, h->s.M, dfit, h->st));
+    stage_end(h, t0, kReduce);
+  }
+  return GAME_OK;
+}
+
+int check_status(game_ctx* h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (st != kDevOk) {
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return fail(GAME_ETIMEOUT, "a kernel wait timed out; results of the affected calls are void");
+  }
+  return GAME_OK;
+}
+
+int validate_params(const game_params& p, const Shape& s, std::string* why) {
+  for (int r : p.reserved)
+    if (r != 0) {
+      *why = "reserved fields must be zero";
+      return 0;
+    }
+  if (p.elitism < 0 || p.elitism > 256) {
+    *why = "elitism must be in 0..256";
+    return 0;
+  }
+  if (p.tournament < 1 || p.tournament > kMaxTournament) {
+    *why = "tournament must be in 1..64";
+    return 0;
+  }
+  if (p.immigrants < 0) {
+    *why = "immigrants must be >= 0";
+    return 0;
+  }
+  const int64_t P = p.P == 0 ? (int64_t)s.B * s.N + 1 : p.P;
+  if (P < (int64_t)p.elitism + p.immigrants + 2 || P > (1 << 24)) {
+    *why = "population size must be >= elitism + immigrants + 2 (and <= 2^24)";
+    return 0;
+  }
+  if (!(p.pc >= 0.f && p.pc <= 1.f) || !(p.pm >= 0.f && p.pm <= 1.f)) {
+    *why = "rates must be in [0, 1]";
+    return 0;
+  }
+  if (!(p.sigma >= 0.f) || !isfinite(p.sigma)) {
+    *why = "sigma must be finite and >= 0";
+    return 0;
+  }
+  if (p.precision != GAME_PREC_FP32 && p.precision != GAME_PREC_BF16) {
+    *why = "unknown precision";
+    return 0;
+  }
+  if (p.check_every < 0) {
+    *why = "check_every must be >= 0";
+    return 0;
+  }
+  return 1;
+}
+
+GaDev ga_dev(const game_ctx* h) {
+  GaDev g;
+  g.P = h->prm.P;
+  g.K = h->s.K;
+  g.E = h->prm.elitism;
+  g.T = h->prm.tournament;
+  g.I = h->prm.immigrants;
+  g.thr_pc = (uint32_t)floor((double)h->prm.pc * 16777216.0);
+  g.thr_pm = (uint32_t)floor((double)h->prm.pm * 16777216.0);
+  g.sigma = h->prm.sigma;
+  return g;
+}
+
+void destroy_ctx(game_ctx* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  harvest_spans(h);
+  dev_free(h->Xt);
+  dev_free(h->y);
+  dev_free(h->pop[0]);
+  dev_free(h->pop[1]);
+  dev_free(h->fit);
+  dev_free(h->plan);
+  dev_free(h->status);
+  dev_free(h->popT);
+  dev_free(h->popA);
+  dev_free(h->a0);
+  dev_free(h->part);
+  dev_free(h->upop);
+  dev_free(h->ufit);
+  delete h;
+}
+
+int copy_in(game_ctx* h, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->st));
+  return GAME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* game_last_error(void) { return g_last_error.c_str(); }
+
+int game_params_default(game_params* out) {
+  if (!out) return fail(GAME_EINVAL, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  out->P = 0;
+  out->elitism = 2;
+  out->tournament = 3;
+  out->precision = GAME_PREC_FP32;
+  out->immigrants = 0;
+  out->check_every = 10;
+  out->pc = 0.9f;
+  out->pm = 0.02f;
+  out->sigma = 0.1f;
+  out->mse_threshold = 0.0;
+  out->seed = 1;
+  return GAME_OK;
+}
+
+int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t degree,
+                int32_t basis, const game_params* prm, void* cuda_stream, game_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(GAME_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!X || !y) return fail(GAME_EINVAL, "X and y must not be NULL");
+  if (M < 1 || N < 1 || degree < 1) return fail(GAME_EINVAL, "M, N and degree must be >= 1");
+  if (basis != GAME_BASIS_CHEB && basis != GAME_BASIS_TRIG)
+    return fail(GAME_EINVAL, "unknown basis");
+  Shape s{};
+  s.M = M;
+  s.Mpad = ((M + 255) / 256) * 256;
+  s.N = N;
+  s.d = degree;
+  s.basis = basis;
+  s.B = basis == GAME_BASIS_TRIG ? 2 : 1;
+  const int64_t K = (int64_t)s.B * N * degree + 1;
+  if (K > kMaxK) return fail(GAME_EINVAL, "K = B*N*d + 1 exceeds 4097 genes");
+  s.K = (int)K;
+  s.Kp = s.K - 1;
+  if ((int64_t)N * s.Mpad > ((int64_t)1 << 36)) return fail(GAME_EINVAL, "training set too large");
+
+  game_params p;
+  if (prm) p = *prm;
+  else game_params_default(&p);
+  std::string why;
+  if (!validate_params(p, s, &why)) return fail(GAME_EINVAL, why);
+  if (p.P == 0) p.P = s.B * N + 1;   // Eq. 4
+
+  game_ctx* h = new (std::nothrow) game_ctx();
+  if (!h) return fail(GAME_ENOMEM, "handle allocation");
+  h->s = s;
+  h->prm = p;
+  h->st = static_cast<cudaStream_t>(cuda_stream);
+  int rc = GAME_OK;
+  auto bail = [&](int code) {
+    destroy_ctx(h);
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+  e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "multiprocessor count"));
+
+  if (dev_alloc(&h->Xt, (size_t)s.Mpad * N) != cudaSuccess ||
+      dev_alloc(&h->y, (size_t)s.Mpad) != cudaSuccess ||
+      dev_alloc(&h->pop[0], (size_t)p.P * s.K) != cudaSuccess ||
+      dev_alloc(&h->pop[1], (size_t)p.P * s.K) != cudaSuccess ||
+      dev_alloc(&h->fit, (size_t)p.P) != cudaSuccess ||
+      dev_alloc(&h->plan, (size_t)p.P) != cudaSuccess ||
+      dev_alloc(&h->status, 4) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(GAME_ENOMEM, "device allocation of the training set / GA state"));
+  }
+  // training set: device copies in the tiled layout, validated on the way
+  const float* dX = X;
+  const float* dy = y;
+  float* tmpX = nullptr;
+  float* tmpy = nullptr;
+  if (!is_device_ptr(X)) {
+    if (dev_alloc(&tmpX, (size_t)M * N) != cudaSuccess)
+      return bail(fail(GAME_ENOMEM, "staging copy of X"));
+    e = cudaMemcpyAsync(tmpX, X, (size_t)M * N * sizeof(float), cudaMemcpyHostToDevice, h->st);
+    dX = tmpX;
+  }
+  if (e == cudaSuccess && !is_device_ptr(y)) {
+    if (dev_alloc(&tmpy, (size_t)M) != cudaSuccess) {
+      dev_free(tmpX);
+      return bail(fail(GAME_ENOMEM, "staging copy of y"));
+    }
+    e = cudaMemcpyAsync(tmpy, y, (size_t)M * sizeof(float), cudaMemcpyHostToDevice, h->st);
+    dy = tmpy;
+  }
+  int bad_h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
+  if (e == cudaSuccess) e = launch_relayout_X(dX, dy, s, h->Xt, h->y, h->status, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bad_h, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  dev_free(tmpX);
+  dev_free(tmpy);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "training-set upload"));
+  if (bad_h[0]) return bail(fail(GAME_EINVAL, "X or y holds NaN or Inf"));
+  if (bad_h[1]) return bail(fail(GAME_EINVAL, "Chebyshev basis needs features in [-1, 1]"));
+
+  // generation 0: uniform genes, then their fitness
+  e = launch_init_population(p.seed, p.P, s.K, h->pop[0], h->st);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "init population"));
+  rc = eval_device(h, h->pop[0], p.P, p.precision, h->fit);
+  if (rc) return bail(rc);
+  rc = check_status(h);
+  if (rc) return bail(rc);
+  h->fit_valid = true;
+  h->gen = 0;
+  *out = h;
+  return GAME_OK;
+}
+
+int game_get_shape(game_t h, int64_t* M, int32_t* N, int32_t* K, int32_t* P) {
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (M) *M = h->s.M;
+  if (N) *N = h->s.N;
+  if (K) *K = h->s.K;
+  if (P) *P = h->prm.P;
+  return GAME_OK;
+}
+
+int game_eval_fitness_prec(game_t h, const float* pop, int32_t P, int32_t precision,
+                           double* fit_out) {
+  g_last_error.clear();
+  if (!h || !pop || !fit_out) return fail(GAME_EINVAL, "NULL argument");
+  if (P < 1 || P > (1 << 24)) return fail(GAME_EINVAL, "P must be in 1..2^24");
+  if (precision != GAME_PREC_FP32 && precision != GAME_PREC_BF16)
+    return fail(GAME_EINVAL, "unknown precision");
+  const bool dev_in = is_device_ptr(pop), dev_out = is_device_ptr(fit_out);
+  if (dev_in != dev_out) return fail(GAME_EINVAL, "pop and fit_out must be in the same memory");
+  if (dev_in) return eval_device(h, pop, P, precision, fit_out);
+  if (P > h->ucap) {
+    dev_free(h->upop);
+    dev_free(h->ufit);
+    h->upop = nullptr;
+    h->ufit = nullptr;
+    h->ucap = 0;
+    if (dev_alloc(&h->upop, (size_t)P * h->s.K) != cudaSuccess ||
+        dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GAME_ENOMEM, "device copy of the population");
+    }
+    h->ucap = P;
+  }
+  CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->s.K * sizeof(float), cudaMemcpyHostToDevice,
+                     h->st));
+  int rc = eval_device(h, h->upop, P, precision, h->ufit);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(fit_out, h->ufit, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return check_status(h);
+}
+
+int game_eval_fitness(game_t h, const float* pop, int32_t P, double* fit_out) {
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  return game_eval_fitness_prec(h, pop, P, h->prm.precision, fit_out);
+}
+
+int game_generation(game_t h, uint64_t seed) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (h->gen >= 0xFFFFFFFFll) return fail(GAME_ESTATE, "generation counter exhausted");
+  int rc;
+  if (!h->fit_valid) {
+    rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+    if (rc) return rc;
+    h->fit_valid = true;
+  }
+  cudaEvent_t t0 = stage_begin(h);
+  CK(launch_generation(ga_dev(h), h->pop[h->cur], h->fit, seed, (uint32_t)h->gen, h->plan,
+                       h->pop[h->cur ^ 1], h->st));
+  stage_end(h, t0, kOperators);
+  h->cur ^= 1;
+  h->gen += 1;
+  h->fit_valid = false;
+  rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+  if (rc) return rc;
+  h->fit_valid = true;
+  return GAME_OK;
+}
+
+int game_train(game_t h, int32_t generations, int32_t* generations_run) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (generations < 0) return fail(GAME_EINVAL, "generations must be >= 0");
+  if (generations_run) *generations_run = 0;
+  const int every = h->prm.check_every > 0 ? h->prm.check_every : 1;
+  const bool use_stop = h->prm.mse_threshold > 0.0;
+  double* fit_h = nullptr;
+  if (use_stop) {
+    fit_h = new (std::nothrow) double[h->prm.P];
+    if (!fit_h) return fail(GAME_ENOMEM, "host fitness buffer");
+  }
+  int rc = GAME_OK;
+  int done = 0;
+  for (; done < generations; ++done) {
+    if (use_stop && done % every == 0) {
+      cudaError_t e = cudaMemcpyAsync(fit_h, h->fit, sizeof(double) * h->prm.P,
+                                      cudaMemcpyDeviceToHost, h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "stop-rule readback");
+        break;
+      }
+      double best = INFINITY;
+      for (int p = 0; p < h->prm.P; ++p)
+        if (fit_h[p] < best) best = fit_h[p];
+      if (best < h->prm.mse_threshold) break;
+    }
+    rc = game_generation(h, h->prm.seed);
+    if (rc) break;
+  }
+  delete[] fit_h;
+  if (generations_run) *generations_run = done;
+  if (rc) return rc;
+  return check_status(h);
+}
+
+int game_get_population(game_t h, float* pop_out, double* fit_out, int64_t* generation) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (generation) *generation = h->gen;
+  bool host = false;
+  if (pop_out) {
+    host |= !is_device_ptr(pop_out);
+    CK(cudaMemcpyAsync(pop_out, h->pop[h->cur], (size_t)h->prm.P * h->s.K * sizeof(float),
+                       cudaMemcpyDefault, h->st));
+  }
+  if (fit_out) {
+    if (!h->fit_valid) {
+      int rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+      if (rc) return rc;
+      h->fit_valid = true;
+    }
+    host |= !is_device_ptr(fit_out);
+    CK(cudaMemcpyAsync(fit_out, h->fit, (size_t)h->prm.P * sizeof(double), cudaMemcpyDefault,
+                       h->st));
+  }
+  if (host) return check_status(h);
+  return GAME_OK;
+}
+
+int game_set_state(game_t h, const float* pop, const double* fit, int64_t generation) {
+  g_last_error.clear();
+  if (!h || !pop) return fail(GAME_EINVAL, "NULL argument");
+  if (generation < 0 || generation >= 0xFFFFFFFFll) return fail(GAME_EINVAL, "bad generation");
+  int rc = copy_in(h, h->pop[h->cur], pop, (size_t)h->prm.P * h->s.K * sizeof(float));
+  if (rc) return rc;
+  if (fit) {
+    rc = copy_in(h, h->fit, fit, (size_t)h->prm.P * sizeof(double));
+    if (rc) return rc;
+  } else {
+    rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+    if (rc) return rc;
+  }
+  h->fit_valid = true;
+  h->gen = generation;
+  return check_status(h);
+}
+
+int game_set_timing(game_t h, int32_t enable) {
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  harvest_spans(h);
+  for (int k = 0; k < 4; ++k) {
+    h->tot_ms[k] = 0.0;
+    h->count[k] = 0;
+  }
+  h->timing = enable != 0;
+  return GAME_OK;
+}
+
+int game_get_timing(game_t h, game_timing* out) {
+  if (!h || !out) return fail(GAME_EINVAL, "NULL argument");
+  harvest_spans(h);
+  out->fitness_ms = h->tot_ms[kFitness];
+  out->pack_ms = h->tot_ms[kPack];
+  out->reduce_ms = h->tot_ms[kReduce];
+  out->operators_ms = h->tot_ms[kOperators];
+  out->fitness_launches = h->count[kFitness];
+  out->pack_launches = h->count[kPack];
+  out->reduce_launches = h->count[kReduce];
+  out->operators_launches = h->count[kOperators];
+  return GAME_OK;
+}
+
+int game_sync(game_t h) {
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  return check_status(h);
+}
+
+int game_destroy(game_t h) {
+  destroy_ctx(h);
+  return GAME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libgame.so (include/game.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Arrays may be numpy arrays (host memory) or torch CUDA tensors
+(device memory); torch supplies device memory and the stream. If the
+library has not been built the import of the functions fails loudly: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GAME_OK = 0
+GAME_EINVAL = -1
+GAME_ENOMEM = -2
+GAME_ECUDA = -3
+GAME_ETIMEOUT = -4
+GAME_ESTATE = -5
+
+GAME_BASIS_CHEB = 0
+GAME_BASIS_TRIG = 1
+GAME_PREC_FP32 = 0
+GAME_PREC_BF16 = 1
+
+_ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
+              GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}
+
+# every symbol include/game.h declares
+EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_fitness",
+            "game_eval_fitness_prec", "game_generation", "game_train", "game_get_population",
+            "game_set_state", "game_set_timing", "game_get_timing", "game_sync",
+            "game_destroy", "game_last_error")
+
+
+class GameError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class game_params(ctypes.Structure):
+    _fields_ = [
+        ("P", ctypes.c_int32),
+        ("elitism", ctypes.c_int32),
+        ("tournament", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("immigrants", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("pc", ctypes.c_float),
+        ("pm", ctypes.c_float),
+        ("sigma", ctypes.c_float),
+        ("reserved_f", ctypes.c_float),
+        ("mse_threshold", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+class game_timing(ctypes.Structure):
+    _fields_ = [
+        ("fitness_ms", ctypes.c_double),
+        ("pack_ms", ctypes.c_double),
+        ("reduce_ms", ctypes.c_double),
+        ("operators_ms", ctypes.c_double),
+        ("fitness_launches", ctypes.c_int64),
+        ("pack_launches", ctypes.c_int64),
+        ("reduce_launches", ctypes.c_int64),
+        ("operators_launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgame.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libgame.so not built at {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, u64, dp = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                             ctypes.c_void_p)
+    sig = {
+        "game_params_default": [ctypes.POINTER(game_params)],
+        "game_create": [vp, vp, i64, i32, i32, i32, ctypes.POINTER(game_params), vp,
+                        ctypes.POINTER(vp)],
+        "game_get_shape": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                           ctypes.POINTER(i32)],
+        "game_eval_fitness": [vp, vp, i32, dp],
+        "game_eval_fitness_prec": [vp, vp, i32, i32, dp],
+        "game_generation": [vp, u64],
+        "game_train": [vp, i32, ctypes.POINTER(i32)],
+        "game_get_population": [vp, vp, dp, ctypes.POINTER(i64)],
+        "game_set_state": [vp, vp, dp, i64],
+        "game_set_timing": [vp, i32],
+        "game_get_timing": [vp, ctypes.POINTER(game_timing)],
+        "game_sync": [vp],
+        "game_destroy": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.game_last_error.argtypes = []
+    lib.game_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != GAME_OK:
+        raise GameError(rc, load().game_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def game_params_default() -> game_params:
+    p = game_params()
+    _check(load().game_params_default(ctypes.byref(p)))
+    return p
+
+
+def game_create(X, y, degree: int, basis: int, prm: game_params | None = None, stream=None):
+    """X [M][N] float32, y [M] float32 (numpy or CUDA tensors)."""
+    M, N = X.shape
+    h = ctypes.c_void_p()
+    _check(load().game_create(_ptr(X), _ptr(y), M, N, degree, basis,
+                              ctypes.byref(prm) if prm is not None else None,
+                              _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def game_get_shape(h):
+    M, N, K, P = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().game_get_shape(h, ctypes.byref(M), ctypes.byref(N), ctypes.byref(K),
+                                 ctypes.byref(P)))
+    return M.value, N.value, K.value, P.value
+
+
+def game_eval_fitness(h, pop, fit_out, precision: int | None = None):
+    """pop [P][K] float32, fit_out [P] float64; both numpy or both CUDA tensors."""
+    P = pop.shape[0]
+    if precision is None:
+        _check(load().game_eval_fitness(h, _ptr(pop), P, _ptr(fit_out)))
+    else:
+        _check(load().game_eval_fitness_prec(h, _ptr(pop), P, precision, _ptr(fit_out)))
+    return fit_out
+
+
+def game_generation(h, seed: int):
+    _check(load().game_generation(h, seed))
+
+
+def game_train(h, generations: int) -> int:
+    run = ctypes.c_int32()
+    _check(load().game_train(h, generations, ctypes.byref(run)))
+    return run.value
+
+
+def game_get_population(h, pop_out=None, fit_out=None) -> int:
+    g = ctypes.c_int64()
+    _check(load().game_get_population(h, _ptr(pop_out), _ptr(fit_out), ctypes.byref(g)))
+    return g.value
+
+
+def game_set_state(h, pop, fit=None, generation: int = 0):
+    _check(load().game_set_state(h, _ptr(pop), _ptr(fit), generation))
+
+
+def game_set_timing(h, enable: bool):
+    _check(load().game_set_timing(h, int(bool(enable))))
+
+
+def game_get_timing(h) -> dict:
+    t = game_timing()
+    _check(load().game_get_timing(h, ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in game_timing._fields_}
+
+
+def game_sync(h):
+    _check(load().game_sync(h))
+
+
+def game_destroy(h):
+    if h:
+        _check(load().game_destroy(h))
+
+
+class Game:
+    """Owning wrapper of a handle with numpy convenience accessors."""
+
+    def __init__(self, X, y, degree, basis=GAME_BASIS_CHEB, stream=None, **params):
+        prm = game_params_default()
+        for k, v in params.items():
+            setattr(prm, k, v)
+        self._keep = (X, y)
+        self.h = game_create(X, y, degree, basis, prm, stream)
+        self.M, self.N, self.K, self.P = game_get_shape(self.h)
+
+    def eval_fitness(self, pop, precision=None):
+        if isinstance(pop, np.ndarray):
+            pop = np.ascontiguousarray(pop, dtype=np.float32)
+            fit = np.zeros(pop.shape[0], dtype=np.float64)
+        else:
+            import torch
+            fit = torch.empty(pop.shape[0], dtype=torch.float64, device=pop.device)
+        return game_eval_fitness(self.h, pop, fit, precision)
+
+    def generation(self, seed):
+        game_generation(self.h, seed)
+
+    def train(self, generations):
+        return game_train(self.h, generations)
+
+    def population(self):
+        pop = np.zeros((self.P, self.K), dtype=np.float32)
+        fit = np.zeros(self.P, dtype=np.float64)
+        g = game_get_population(self.h, pop, fit)
+        return pop, fit, g
+
+    def set_state(self, pop, fit=None, generation=0):
+        pop = np.ascontiguousarray(pop, dtype=np.float32) if isinstance(pop, np.ndarray) else pop
+        if fit is not None and isinstance(fit, np.ndarray):
+            fit = np.ascontiguousarray(fit, dtype=np.float64)
+        game_set_state(self.h, pop, fit, generation)
+
+    def sync(self):
+        game_sync(self.h)
+
+    def set_timing(self, enable=True):
+        game_set_timing(self.h, enable)
+
+    def timing(self):
+        return game_get_timing(self.h)
+
+    def close(self):
+        if self.h:
+            game_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

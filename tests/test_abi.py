@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/game.h declares; argument checks that precede any GPU work reject
+bad shapes without a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1211_5481_gb300 import build as gbuild
+from paper_1211_5481_gb300 import game
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "game.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(game_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_header_symbols():
+    lib = gbuild.build()
+    assert os.path.exists(lib)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (game_[a-z_0-9]+)$", out, flags=re.M))
+    decl = declared_symbols()
+    assert decl, "no declarations parsed"
+    missing = [s for s in decl if s not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    assert set(decl) == set(game.EXPORTED)
+
+
+def test_build_targets_sm103a_only():
+    assert gbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_host_side_argument_checks():
+    lib = game.load()
+    p = game.game_params_default()
+    assert p.elitism == 2 and p.tournament == 3 and abs(p.pc - 0.9) < 1e-7
+    h = ctypes.c_void_p()
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.zeros(4, dtype=np.float32)
+    for M, N, d, basis in [(0, 2, 3, 0), (4, 0, 3, 0), (4, 2, 0, 0), (4, 2, 3, 7)]:
+        rc = lib.game_create(X.ctypes.data, y.ctypes.data, M, N, d, basis, None, None,
+                             ctypes.byref(h))
+        assert rc == game.GAME_EINVAL
+        assert lib.game_last_error()
+    # K above the supported maximum
+    rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2049, 2, 0, None, None,
+                         ctypes.byref(h))
+    assert rc == game.GAME_EINVAL
+    bad = game.game_params_default()
+    bad.P = 3   # < elitism + 2
+    rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
+                         ctypes.byref(h))
+    assert rc == game.GAME_EINVAL
+    bad = game.game_params_default()
+    bad.tournament = 0
+    rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
+                         ctypes.byref(h))
+    assert rc == game.GAME_EINVAL
+    assert lib.game_destroy(None) == game.GAME_OK

@@ -1,0 +1,142 @@
+"""Parity of the CUDA fitness kernels with the FP64 oracle, through the C ABI.
+
+FP32 form (CUDA-core FFMA): |f - f_oracle| <= 1e-5 |f_oracle| + 1e-7 mean(y^2).
+BF16 form (tcgen05): within the worst-case rounding bound of a BF16 x BF16 ->
+FP32 contraction (helpers.bf16_bound), and its relative error is reported.
+"""
+import numpy as np
+import pytest
+
+from helpers import CHEB, TRIG, bf16_bound, fp32_tol
+from paper_1211_5481_gb300 import datagen as dg
+from paper_1211_5481_gb300 import game
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FP32, BF16 = game.GAME_PREC_FP32, game.GAME_PREC_BF16
+
+# (M, N, d, basis, P): tile multiples, ragged tails, K not a multiple of 16,
+# P below / above / not a multiple of 128, tiny and long contractions
+CASES = [
+    (2000, 8, 4, CHEB, 64),      # the small regression workload's shape
+    (1003, 5, 3, CHEB, 70),      # K' = 15
+    (777, 3, 7, TRIG, 130),      # trigonometric, P just above one tile
+    (300, 1, 1, CHEB, 3),        # K = 2
+    (1, 4, 2, CHEB, 5),          # a single pattern
+    (5000, 16, 10, TRIG, 257),   # K' = 320, 6 K-blocks
+    (4099, 40, 8, CHEB, 1),      # a single chromosome, K' = 320
+    (513, 64, 10, TRIG, 33),     # K' = 1280, the longest batched contraction
+    (6000, 32, 8, CHEB, 256),    # the large classification shape, reduced M
+]
+
+
+def make_problem(M, N, d, basis, seed):
+    pr = dg.regression(seed, M, N, min(d, 4), 0.05, degree=d, basis=basis)
+    return pr
+
+
+@pytest.fixture(scope="module")
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    game.load()
+    return torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("case", CASES, ids=[str(c) for c in CASES])
+@pytest.mark.parametrize("prec", [FP32, BF16], ids=["fp32", "bf16"])
+def test_fitness_matches_oracle(orc, dev, case, prec):
+    M, N, d, basis, P = case
+    pr = make_problem(M, N, d, basis, seed=M + N + d)
+    pop = dg.random_population(7 + P, P, pr.K)
+    ref = orc.fitness(pr.X, pr.y, pop, d, basis)
+    with game.Game(pr.X, pr.y, d, basis, P=max(P, 4), precision=prec) as g:
+        got = g.eval_fitness(pop)
+    if prec == FP32:
+        tol = fp32_tol(ref, pr.y)
+    else:
+        tol = bf16_bound(ref, pr.X, pop, d, basis)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (f"max err {err.max():.3e}, worst ratio "
+                                f"{(err / tol).max():.3f}, rel {np.max(err / np.abs(ref)):.3e}")
+
+
+def test_device_and_host_pointers_agree(dev):
+    pr = dg.small_regression()
+    pop = dg.random_population(3, 64, pr.K)
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    with game.Game(Xd, yd, pr.degree, CHEB, P=64) as g:
+        host = g.eval_fitness(pop)
+        dfit = g.eval_fitness(torch.from_numpy(pop).to(dev))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host, dfit.cpu().numpy())
+
+
+def test_converged_population(orc, dev):
+    """Near the generating coefficients the MSE is ~ noise^2 = 0.0025 and
+    the residual sum cancels most: the FP32 bound still holds."""
+    pr = dg.small_regression()
+    rng = np.random.default_rng(5)
+    pop = (pr.coef[None, :] + rng.normal(0, 0.01, (64, pr.K))).astype(np.float32)
+    pop[0] = pr.coef
+    ref = orc.fitness(pr.X, pr.y, pop, pr.degree, CHEB)
+    assert ref.min() < 0.003
+    with game.Game(pr.X, pr.y, pr.degree, CHEB, P=64) as g:
+        got = g.eval_fitness(pop)
+        got_bf = g.eval_fitness(pop, precision=BF16)
+    assert np.all(np.abs(got - ref) <= fp32_tol(ref, pr.y))
+    assert np.all(np.abs(got_bf - ref) <= bf16_bound(ref, pr.X, pop, pr.degree, CHEB))
+
+
+def test_deterministic(dev):
+    pr = dg.regression(5, 3000, 12, 4, 0.05, degree=5)
+    pop = dg.random_population(4, 200, pr.K)
+    for prec in (FP32, BF16):
+        with game.Game(pr.X, pr.y, 5, CHEB, P=200, precision=prec) as g:
+            a = g.eval_fitness(pop)
+            b = g.eval_fitness(pop)
+        np.testing.assert_array_equal(a, b)
+
+
+def test_full_size_sampled(orc, dev):
+    """The large classification workload at full size (M = 10^6, N = 32,
+    degree 8, P = 1024) in the benchmark's launch configuration; a sample of
+    chromosomes is re-computed by the oracle one by one."""
+    pr = dg.large_classification()
+    P = 1024
+    pop = orc.init_population(2, P, pr.K)
+    sample = np.array([0, 1, 127, 128, 511, 640, 1000, 1023])
+    ref = orc.fitness(pr.X, pr.y, pop[sample], pr.degree, CHEB)
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    with game.Game(Xd, yd, pr.degree, CHEB, P=P) as g:
+        f32 = g.eval_fitness(pop)
+        fbf = g.eval_fitness(pop, precision=BF16)
+    assert np.all(np.abs(f32[sample] - ref) <= fp32_tol(ref, pr.y))
+    bound = bf16_bound(ref, pr.X[::50], pop[sample], pr.degree, CHEB)
+    # the bound uses every 50th pattern for its mean of S^2: allow 10% for that
+    assert np.all(np.abs(fbf[sample] - ref) <= 1.1 * bound)
+    # all chromosomes: the two GPU forms agree within the BF16 bound scale
+    rel = np.abs(fbf - f32) / f32
+    assert np.median(rel) < 1e-2
+
+
+def test_create_rejects_bad_data(dev):
+    pr = dg.regression(3, 500, 4, 3, 0.0, degree=3)
+    X = pr.X.copy()
+    X[7, 2] = np.nan
+    with pytest.raises(game.GameError) as ei:
+        game.Game(X, pr.y, 3, CHEB, P=10)
+    assert ei.value.code == game.GAME_EINVAL
+    X = pr.X.copy()
+    X[3, 1] = 1.5
+    with pytest.raises(game.GameError) as ei:
+        game.Game(X, pr.y, 3, CHEB, P=10)
+    assert ei.value.code == game.GAME_EINVAL
+    with game.Game(X, pr.y, 3, TRIG, P=10) as g:   # any x is in the trigonometric domain
+        assert g.K == 2 * 4 * 3 + 1
+    y = pr.y.copy()
+    y[0] = np.inf
+    with pytest.raises(game.GameError):
+        game.Game(pr.X, y, 3, CHEB, P=10)

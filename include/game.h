@@ -151,6 +151,30 @@ int game_set_timing(game_t h, int32_t enable);
 /* Synchronises the stream and returns the totals since the last enable. */
 int game_get_timing(game_t h, game_timing* out);
 
+/* Fitness of a population without any device allocation, for callers that
+ * cannot call cudaMalloc: code running while another component captures the
+ * stream into a CUDA graph, plug-ins confined to a host application's fixed
+ * device-memory budget, runtimes that forbid allocation after start-up. The
+ * paper has no counterpart of this call; it is a deployment variant of the
+ * FP32 form of game_eval_fitness (same Eq. 2 / Eq. 3 MSE, FP32 CUDA-core
+ * contraction, FP64 cross-tile sum) that needs no handle.
+ *   X [M][N] FP32 row-major, y [M] FP32, pop [P][K] FP32 (K = B*N*d + 1),
+ *   fit_out [P] FP64: all device pointers on the current device, owned by
+ *   the caller. Inputs are used as given (no NaN / domain checks).
+ *   cuda_stream: a cudaStream_t or NULL. Only enqueues work.
+ * The only intermediate buffer is a fixed 4 MiB array of FP64 partial sums
+ * that the library holds on every GPU that loads it, until the process
+ * exits. P above 524288 (the array's capacity in chromosome rows) is
+ * rejected with GAME_EINVAL before any launch. The first call on a device
+ * looks up that array's address (do it before any stream capture). All
+ * calls share the array: calls that overlap on the GPU race on it, so the
+ * caller must serialise them. Errors: GAME_EINVAL (arguments, host
+ * pointers), GAME_ECUDA; the reason is in game_last_error(). */
+int game_eval_fitness_static(const float* X, const float* y, int64_t M,
+                             int32_t N, int32_t degree, int32_t basis,
+                             const float* pop, int32_t P, double* fit_out,
+                             void* cuda_stream);
+
 /* Waits for the handle's stream and reports a kernel timeout, if any. */
 int game_sync(game_t h);
 

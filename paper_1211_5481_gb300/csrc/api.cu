@@ -17,6 +17,16 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+namespace game {
+// Sets the calling thread's game_last_error() text (used by entry points
+// defined outside this file).
+void record_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace game
+
+namespace {
+
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;

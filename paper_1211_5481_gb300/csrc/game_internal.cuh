@@ -62,6 +62,8 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms);
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0, int P,
                               int Ppad, double* part, int* status, cudaStream_t st);
+// api.cu
+void record_error(const char* msg);
 // reduce.cu
 cudaError_t launch_reduce(const double* part, int rows, int P, int Ppad, int64_t M,
                           double* fit, cudaStream_t st);

@@ -34,7 +34,7 @@ _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA
 EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_fitness",
             "game_eval_fitness_prec", "game_generation", "game_train", "game_get_population",
             "game_set_state", "game_set_timing", "game_get_timing", "game_sync",
-            "game_destroy", "game_last_error")
+            "game_destroy", "game_last_error", "game_eval_fitness_static")
 
 
 class GameError(RuntimeError):
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         "game_get_timing": [vp, ctypes.POINTER(game_timing)],
         "game_sync": [vp],
         "game_destroy": [vp],
+        "game_eval_fitness_static": [vp, vp, i64, i32, i32, i32, vp, i32, dp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +206,14 @@ def game_get_timing(h) -> dict:
     t = game_timing()
     _check(load().game_get_timing(h, ctypes.byref(t)))
     return {name: getattr(t, name) for name, _ in game_timing._fields_}
+
+
+def game_eval_fitness_static(X, y, degree: int, basis: int, pop, fit_out, stream=None):
+    """Allocation-free FP32 fitness; all arrays are CUDA tensors."""
+    M, N = X.shape
+    _check(load().game_eval_fitness_static(_ptr(X), _ptr(y), M, N, degree, basis, _ptr(pop),
+                                           pop.shape[0], _ptr(fit_out), _stream_ptr(stream)))
+    return fit_out
 
 
 def game_sync(h):

@@ -10,22 +10,29 @@
 // tile's expansion (patterns on MMA-N).
 //
 // Persistent CTAs, one per SM, each walking pattern tiles t = blockIdx.x +
-// i * gridDim.x. Warp roles:
+// i * gridDim.x. Warp roles (16 warps):
 //   warp 0       A producer: bulk-copies 16 KB gene blocks (chromosome tile c,
-//                K-block kb) from the pre-swizzled operand image into a
-//                4-stage ring.
+//                K-block kb of 64 columns) from the pre-swizzled operand
+//                image into a ring of 3-4 stages.
 //   warp 1       MMA issuer (one thread) and tensor-memory owner; two FP32
 //                accumulators of BN columns, so the epilogue of chromosome
-//                tile c overlaps the MMAs of tile c+1.
+//                tile c overlaps the MMAs of tile c+1. The tcgen05 queue
+//                drains fast, so the issuing path is kept minimal: precomputed
+//                descriptors, unrolled groups of four K=16 MMAs, K-blocks taken
+//                in pairs.
 //   warp 2       X producer: bulk-copies the next pattern tile's features.
-//   warps 4-7    epilogue: tcgen05.ld of the accumulator (thread = chromosome,
-//                TMEM lane), r = (y_m - a_0) - D, sse += r^2 over the tile's
-//                patterns in FP32, then added into an FP64 per-CTA partial.
-//   warps 8-11   expansion: the basis recurrences in registers from the
-//                staged features, converted to BF16 and stored in the
-//                K-major SWIZZLE_128B operand layout, one K-block (64
-//                columns) at a time so the next tile's expansion overwrites a
-//                K-block as soon as the last MMA reading it has completed.
+//   warps 4-11   epilogue: tcgen05.ld of the accumulator (thread = chromosome
+//                = TMEM lane; warps 4-7 take the first half of the columns,
+//                8-11 the second), r = (y_m - a_0) - D, sse += r^2 in packed
+//                FP32 pairs, then added to an FP64 partial per (CTA, half).
+//   warps 12-15  expansion: each thread owns fixed pattern rows; per 8-column
+//                chunk (a table built once per launch says where the chunk
+//                starts in the feature / degree sequence) the basis
+//                recurrence runs in registers from the staged features, is
+//                rounded to BF16 and stored in the K-major SWIZZLE_128B
+//                operand layout. K-block kb of the next tile is written as
+//                soon as the last MMA reading K-block kb of this tile has
+//                completed, so the expansion overlaps the MMAs.
 // PHI and D never leave the SM. All waits are bounded (2 s): on expiry the
 // kernel raises a status word, abandons its loops, waits for its own bulk
 // copies and MMAs in flight, frees tensor memory and returns.
@@ -33,24 +40,27 @@
 #include "game_internal.cuh"
 #include "tc_ptx.cuh"
 
+
 namespace game {
 
 namespace {
 
-constexpr int kStages = 4;
 constexpr uint32_t kABytes = 128 * 128;   // one (chromosome tile, K-block) gene block
-constexpr int kWarps = 12;
+constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
-constexpr int kEpiThreads = 128;          // warps 4..7
-constexpr int kBasisThreads = 128;        // warps 8..11
+constexpr int kEpiWarp0 = 4;
+constexpr int kEpiThreads = 256;          // warps 4..11
+constexpr int kBasisWarp0 = 12;
+constexpr int kBasisThreads = 128;        // warps 12..15
 constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr uint32_t kSuspendNs = 20000;     // per try_wait suspension (woken early on completion)
 constexpr int kMaxSmem = 232448;          // 227 KB opt-in per CTA
 constexpr int kMinSmem = 120 * 1024;
 
 struct TcArgs {
   int64_t M;
   int N, d, basis, Kp;
-  int BN, KB, C, nmma_last, ntiles, Ppad, tmem_cols;
+  int BN, KB, C, stages, nmma_last, ntiles, Ppad, tmem_cols;
   const float* Xt;
   const float* y;
   const uint8_t* popA;
@@ -59,26 +69,38 @@ struct TcArgs {
   int* status;
 };
 
-__host__ __device__ inline int phi_bytes(int KB, int BN) { return KB * BN * 128; }
-__host__ __device__ inline int xs_bytes(int N, int BN) { return N * BN * 4; }
-__host__ __device__ inline int num_bars(int KB) { return 2 * kStages + 2 * KB + 7; }
-__host__ __device__ inline int smem_total(int KB, int BN, int N) {
-  return 1024 + phi_bytes(KB, BN) + kStages * (int)kABytes + xs_bytes(N, BN) + 8 +
-         num_bars(KB) * 8 + 16;
+struct SmemPlan {
+  int phi, ast, xs, tab, bars, total;
+};
+
+__host__ __device__ inline int num_bars(int KB, int stages) { return 2 * stages + 2 * KB + 7; }
+
+// Byte offsets of the shared-memory regions from the 1024-aligned base.
+__host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages) {
+  SmemPlan s;
+  s.phi = 0;
+  s.ast = s.phi + KB * BN * 128;
+  s.xs = s.ast + stages * (int)kABytes;
+  s.tab = s.xs + N * BN * 4;
+  s.bars = (s.tab + KB * 8 * 4 + 7) & ~7;
+  s.total = s.bars + num_bars(KB, stages) * 8 + 16 + 1024;   // + alignment slack
+  return s;
 }
 
+// Bounded wait for the phase of the given parity. Waiting threads are
+// suspended by the hardware (suspend-time hint) instead of spinning, so they
+// take no issue slots from the MMA issuer and the producers on their SM
+// sub-partition; each wake-up re-checks the abort flag and the time limit.
 __device__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
   if (ptx::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = ptx::global_timer_ns();
-  for (uint32_t n = 0;; ++n) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
-    if ((n & 15) == 15) {
-      if (*abort_flag) return false;
-      if (ptx::global_timer_ns() - t0 > kTimeoutNs) {
-        *abort_flag = 1;
-        atomicExch(status, (int)kDevTimeout);
-        return false;
-      }
+  for (;;) {
+    if (ptx::mbar_try_wait_sleep(bar, parity, kSuspendNs)) return true;
+    if (*abort_flag) return false;
+    if (ptx::global_timer_ns() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      atomicExch(status, (int)kDevTimeout);
+      return false;
     }
   }
 }
@@ -95,19 +117,37 @@ __device__ void wait_bar_drain(uint32_t bar, uint32_t parity, int* status) {
   }
 }
 
+// sse += ((y - bias) - acc)^2 over 32 columns, two columns per packed op.
+__device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* yc,
+                                          uint64_t bias2, uint64_t& s2) {
+#pragma unroll
+  for (int e4 = 0; e4 < 8; ++e4) {
+    const float4 yv = __ldg(reinterpret_cast<const float4*>(yc) + e4);
+    const uint64_t ya = ptx::f2_sub(ptx::f2_pack(yv.x, yv.y), bias2);
+    const uint64_t yb = ptx::f2_sub(ptx::f2_pack(yv.z, yv.w), bias2);
+    const uint64_t ra = ptx::f2_sub(ya, ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]),
+                                                     __uint_as_float(v[4 * e4 + 1])));
+    const uint64_t rb = ptx::f2_sub(yb, ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]),
+                                                     __uint_as_float(v[4 * e4 + 3])));
+    s2 = ptx::f2_fma(ra, ra, s2);
+    s2 = ptx::f2_fma(rb, rb, s2);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int BN = a.BN, KB = a.KB, N = a.N;
-  uint8_t* phi = base;
-  uint8_t* ast = phi + phi_bytes(KB, BN);
-  float* xs = reinterpret_cast<float*>(ast + kStages * kABytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(xs + (size_t)N * BN) + 7) & ~static_cast<uintptr_t>(7));
+  const int BN = a.BN, KB = a.KB, N = a.N, S = a.stages;
+  const SmemPlan sp = smem_plan(KB, BN, N, S);
+  uint8_t* phi = base + sp.phi;
+  uint8_t* ast = base + sp.ast;
+  float* xs = reinterpret_cast<float*>(base + sp.xs);
+  uint32_t* tab = reinterpret_cast<uint32_t*>(base + sp.tab);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + sp.bars);
   uint64_t* a_full = bars;
-  uint64_t* a_empty = a_full + kStages;
-  uint64_t* phi_full = a_empty + kStages;
+  uint64_t* a_empty = a_full + S;
+  uint64_t* phi_full = a_empty + S;
   uint64_t* phi_free = phi_full + KB;
   uint64_t* acc_full = phi_free + KB;
   uint64_t* acc_empty = acc_full + 2;
@@ -119,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       ptx::mbar_init(ptx::smem_addr(&a_full[s]), 1);
       ptx::mbar_init(ptx::smem_addr(&a_empty[s]), 1);
     }
@@ -154,63 +194,103 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   if (warp == 0) {
     // ---------------- A producer ----------------
     if (lane == 0) {
-      uint32_t q = 0;
+      uint32_t q = 0, s = 0, ph = 0;   // issue count, stage, stage phase
       bool ok = true;
       for (int it = 0; it < my_tiles && ok; ++it)
         for (int c = 0; c < a.C && ok; ++c)
           for (int kb = 0; kb < KB && ok; ++kb) {
-            const uint32_t s = q % kStages, u = q / kStages;
-            ok = wait_bar(ptx::smem_addr(&a_empty[s]), (u & 1) ^ 1, abort_flag, a.status);
+            ok = wait_bar(ptx::smem_addr(&a_empty[s]), ph ^ 1, abort_flag, a.status);
             if (!ok) break;
             ptx::mbar_arrive_expect_tx(ptx::smem_addr(&a_full[s]), kABytes);
             ptx::bulk_g2s(ptx::smem_addr(ast + s * kABytes),
                           a.popA + (size_t)(c * KB + kb) * kABytes, kABytes,
                           ptx::smem_addr(&a_full[s]));
             ++q;
+            if (++s == (uint32_t)S) {
+              s = 0;
+              ph ^= 1;
+            }
           }
       // own copies in flight: the last phase armed on each stage
-      for (uint32_t s = 0; s < kStages && s < q; ++s) {
-        const uint32_t uses = (q - s + kStages - 1) / kStages;
-        wait_bar_drain(ptx::smem_addr(&a_full[s]), (uses - 1) & 1, a.status);
+      for (uint32_t st = 0; st < (uint32_t)S && st < q; ++st) {
+        const uint32_t uses = (q - st + S - 1) / S;
+        wait_bar_drain(ptx::smem_addr(&a_full[st]), (uses - 1) & 1, a.status);
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
+    // The tcgen05 MMA queue drains quickly, so this thread's path between
+    // MMAs is kept short: descriptors are precomputed (a stage, a K-block or
+    // a K=16 step only moves the 14-bit start-address field), K-blocks are
+    // taken in pairs (both operand waits first, then up to eight MMAs back
+    // to back, then the commits), and the inner groups are unrolled.
     if (lane == 0) {
       const uint32_t idesc = ptx::idesc_bf16_f32(128, BN);
-      const uint32_t phi_base = ptx::smem_addr(phi), ast_base = ptx::smem_addr(ast);
-      uint32_t q = 0, acc_it = 0;
+      const uint64_t adesc0 = ptx::desc_kmajor_sw128(ptx::smem_addr(ast));
+      const uint64_t bdesc0 = ptx::desc_kmajor_sw128(ptx::smem_addr(phi));
+      const uint32_t a_step = kABytes >> 4;                  // one A stage
+      const uint32_t b_step = (uint32_t)(BN * 128) >> 4;     // one expansion K-block
+      const uint32_t a_full0 = ptx::smem_addr(a_full), a_empty0 = ptx::smem_addr(a_empty);
+      const uint32_t phi_full0 = ptx::smem_addr(phi_full), phi_free0 = ptx::smem_addr(phi_free);
+      const uint32_t acc_full0 = ptx::smem_addr(acc_full), acc_empty0 = ptx::smem_addr(acc_empty);
+      const int nlast = a.nmma_last;
+      uint32_t s = 0, ph = 0, acc_it = 0;   // A stage and its phase, accumulator count
       bool ok = true;
+      // issues the MMAs of one K-block (nm of 4 K=16 steps)
+      auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int nm) {
+        const uint64_t ad = adesc0 + st * a_step;
+        const uint64_t bd = bdesc0 + (uint32_t)kb * b_step;
+        if (nm == 4) {
+          ptx::mma_bf16(d_tmem, ad, bd, idesc, kb != 0);
+          ptx::mma_bf16(d_tmem, ad + 2u, bd + 2u, idesc, 1u);
+          ptx::mma_bf16(d_tmem, ad + 4u, bd + 4u, idesc, 1u);
+          ptx::mma_bf16(d_tmem, ad + 6u, bd + 6u, idesc, 1u);
+        } else {
+          for (int kk = 0; kk < nm; ++kk)
+            ptx::mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+        }
+      };
       for (int it = 0; it < my_tiles && ok; ++it) {
         for (int c = 0; c < a.C && ok; ++c) {
           const uint32_t buf = acc_it & 1, u = acc_it >> 1;
-          ok = wait_bar(ptx::smem_addr(&acc_empty[buf]), (u & 1) ^ 1, abort_flag, a.status);
+          ok = wait_bar(acc_empty0 + 8 * buf, (u & 1) ^ 1, abort_flag, a.status);
           if (!ok) break;
           ptx::tc_fence_after();
           const uint32_t d_tmem = tmem + buf * (uint32_t)BN;
-          for (int kb = 0; kb < KB; ++kb) {
+          for (int kb = 0; kb < KB && ok; kb += 2) {
+            const bool two = kb + 1 < KB;
+            uint32_t s1 = s + 1, ph1 = ph;
+            if (s1 == (uint32_t)S) {
+              s1 = 0;
+              ph1 ^= 1;
+            }
+            // operands of both K-blocks first
             if (c == 0) {
-              ok = wait_bar(ptx::smem_addr(&phi_full[kb]), it & 1, abort_flag, a.status);
-              if (!ok) break;
-              ptx::tc_fence_after();
+              ok = wait_bar(phi_full0 + 8 * kb, it & 1, abort_flag, a.status);
+              if (ok && two) ok = wait_bar(phi_full0 + 8 * (kb + 1), it & 1, abort_flag, a.status);
             }
-            const uint32_t s = q % kStages;
-            ok = wait_bar(ptx::smem_addr(&a_full[s]), (q / kStages) & 1, abort_flag, a.status);
+            if (ok) ok = wait_bar(a_full0 + 8 * s, ph, abort_flag, a.status);
+            if (ok && two) ok = wait_bar(a_full0 + 8 * s1, ph1, abort_flag, a.status);
             if (!ok) break;
-            ptx::tc_fence_after();
-            const int nm = (kb == KB - 1) ? a.nmma_last : 4;
-            for (int kk = 0; kk < nm; ++kk) {
-              const uint64_t adesc = ptx::desc_kmajor_sw128(ast_base + s * kABytes + kk * 32);
-              const uint64_t bdesc =
-                  ptx::desc_kmajor_sw128(phi_base + (uint32_t)(kb * BN * 128) + kk * 32);
-              ptx::mma_bf16(d_tmem, adesc, bdesc, idesc, (kb | kk) != 0);
+            kblock(d_tmem, s, kb, (kb == KB - 1) ? nlast : 4);
+            if (two) kblock(d_tmem, s1, kb + 1, (kb + 1 == KB - 1) ? nlast : 4);
+            ptx::mma_commit(a_empty0 + 8 * s);
+            if (two) ptx::mma_commit(a_empty0 + 8 * s1);
+            if (c == a.C - 1) {
+              ptx::mma_commit(phi_free0 + 8 * kb);
+              if (two) ptx::mma_commit(phi_free0 + 8 * (kb + 1));
             }
-            ptx::mma_commit(ptx::smem_addr(&a_empty[s]));
-            if (c == a.C - 1) ptx::mma_commit(ptx::smem_addr(&phi_free[kb]));
-            ++q;
+            s = s1;
+            ph = ph1;
+            if (two) {
+              if (++s == (uint32_t)S) {
+                s = 0;
+                ph ^= 1;
+              }
+            }
           }
           if (!ok) break;
-          ptx::mma_commit(ptx::smem_addr(&acc_full[buf]));
+          ptx::mma_commit(acc_full0 + 8 * buf);
           ++acc_it;
         }
       }
@@ -225,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       for (int it = 0; it < my_tiles; ++it) {
         const int64_t t = (int64_t)blockIdx.x + (int64_t)it * G;
         if (!wait_bar(ptx::smem_addr(x_empty), (it & 1) ^ 1, abort_flag, a.status)) break;
-        const uint32_t bytes = (uint32_t)xs_bytes(N, BN);
+        const uint32_t bytes = (uint32_t)(N * BN * 4);
         ptx::mbar_arrive_expect_tx(ptx::smem_addr(x_full), bytes);
         const int64_t m0 = t * BN;
         if (BN >= kPatBlock) {
@@ -242,19 +322,23 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       }
       if (issued > 0) wait_bar_drain(ptx::smem_addr(x_full), (issued - 1) & 1, a.status);
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= kEpiWarp0 && warp < kBasisWarp0) {
     // ---------------- epilogue ----------------
     const int qw = warp & 3;
+    const int half = (warp - kEpiWarp0) >> 2;
     const int row = qw * 32 + lane;
+    const int NH = BN >= 64 ? 2 : 1;          // column halves in use
+    const int HW = BN / NH;                   // columns per half (>= 32)
+    const int col_lo = half * HW;
     const uint32_t lane_addr = (uint32_t)(qw * 32) << 16;
-    double* part_row = a.part + (size_t)blockIdx.x * a.Ppad;
+    double* part_row = a.part + (size_t)(2 * blockIdx.x + half) * a.Ppad;
     uint32_t acc_it = 0;
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
       const int64_t m0 = ((int64_t)blockIdx.x + (int64_t)it * G) * BN;
-      const int64_t rem = a.M - m0;
-      const int valid = rem <= 0 ? 0 : (rem >= BN ? BN : (int)rem);
-      const float* yt = a.y + m0;
+      const int64_t rem = a.M - m0 - col_lo;
+      const int valid = (half >= NH || rem <= 0) ? 0 : (rem >= HW ? HW : (int)rem);
+      const float* yt = a.y + m0 + col_lo;
       for (int c = 0; c < a.C; ++c) {
         const uint32_t buf = acc_it & 1, u = acc_it >> 1;
         ok = wait_bar(ptx::smem_addr(&acc_full[buf]), u & 1, abort_flag, a.status);
@@ -262,44 +346,76 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         ptx::tc_fence_after();
         const int chrom = c * 128 + row;
         const float bias = a.a0[chrom];
-        float s0 = 0.f, s1 = 0.f;
-        for (int col0 = 0; col0 < valid; col0 += 32) {
-          uint32_t v[32];
-          ptx::tmem_ld32(tmem + lane_addr + buf * (uint32_t)BN + (uint32_t)col0, v);
-          if (col0 + 32 <= valid) {
-#pragma unroll
-            for (int e4 = 0; e4 < 8; ++e4) {
-              const float4 yv = __ldg(reinterpret_cast<const float4*>(yt + col0) + e4);
-              const float r0 = (yv.x - bias) - __uint_as_float(v[4 * e4 + 0]);
-              const float r1 = (yv.y - bias) - __uint_as_float(v[4 * e4 + 1]);
-              const float r2 = (yv.z - bias) - __uint_as_float(v[4 * e4 + 2]);
-              const float r3 = (yv.w - bias) - __uint_as_float(v[4 * e4 + 3]);
-              s0 = fmaf(r0, r0, s0);
-              s1 = fmaf(r1, r1, s1);
-              s0 = fmaf(r2, r2, s0);
-              s1 = fmaf(r3, r3, s1);
+        const uint64_t bias2 = ptx::f2_pack(bias, bias);
+        uint64_t s2 = 0;   // two FP32 partial sums (even / odd columns)
+        float s_tail = 0.f;
+        const uint32_t tbase = tmem + lane_addr + buf * (uint32_t)BN + (uint32_t)col_lo;
+        const int nfull = valid / 32;
+        if (nfull > 0) {
+          // double-buffered: the load of chunk k+1 is in flight while chunk k
+          // is reduced
+          uint32_t va[32], vb[32];
+          ptx::tmem_ld32_issue(tbase, va);
+          ptx::tmem_ld32_wait(va);
+          for (int k = 0; k < nfull; k += 2) {
+            const bool has_b = k + 1 < nfull;
+            if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
+            epi_chunk(va, yt + k * 32, bias2, s2);
+            if (has_b) {
+              ptx::tmem_ld32_wait(vb);
+              const bool has_a = k + 2 < nfull;
+              if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
+              epi_chunk(vb, yt + (k + 1) * 32, bias2, s2);
+              if (has_a) ptx::tmem_ld32_wait(va);
             }
-          } else {
-            const int lim = valid - col0;
+          }
+        }
+        if (nfull * 32 < valid) {   // ragged last chunk of the last tile
+          uint32_t v[32];
+          ptx::tmem_ld32(tbase + (uint32_t)nfull * 32, v);
+          const int lim = valid - nfull * 32;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              if (e < lim) {
-                const float r = (yt[col0 + e] - bias) - __uint_as_float(v[e]);
-                s0 = fmaf(r, r, s0);
-              }
+          for (int e = 0; e < 32; ++e) {
+            if (e < lim) {
+              const float r = (yt[nfull * 32 + e] - bias) - __uint_as_float(v[e]);
+              s_tail = fmaf(r, r, s_tail);
             }
           }
         }
         ptx::tc_fence_before();
         ptx::mbar_arrive(ptx::smem_addr(&acc_empty[buf]));
-        const double tile_sse = (double)s0 + (double)s1;
+        const float2 sp2 = ptx::f2_unpack(s2);
+        const double tile_sse = (double)sp2.x + (double)sp2.y + (double)s_tail;
         part_row[chrom] = (it == 0) ? tile_sse : part_row[chrom] + tile_sse;
         ++acc_it;
       }
     }
-  } else if (warp >= 8) {
+  } else if (warp >= kBasisWarp0) {
     // ---------------- expansion (basis) ----------------
-    const int bt = threadIdx.x - 8 * 32;
+    const int bt = threadIdx.x - kBasisWarp0 * 32;
+    for (int cid = bt; cid < KB * 8; cid += kBasisThreads)
+      tab[cid] = chunk_desc(cid, a.basis, a.d, a.Kp);
+    ptx::named_bar(1, kBasisThreads);
+    // thread -> rows r0 + 128 * rr (rr < R) and chunks q0, q0 + QS, ...
+    const int RW = BN < 128 ? BN : 128;
+    const int R = BN / RW;          // rows per thread (2 when BN = 256)
+    const int QS = 128 / RW;        // chunk stride (1 when BN >= 128)
+    const int r0 = bt % RW, q0 = bt / RW;
+    const float* xrow0 = xs + (r0 >> 7) * N * XW + (r0 % XW);
+    const float* xrow1 = xs + ((r0 + 128) >> 7) * N * XW + ((r0 + 128) % XW);
+    // one chunk of one row: expansion, BF16 rounding, swizzled 16-byte store
+    auto emit = [&](uint8_t* phik, uint32_t desc, int qd, int r, const float* xr) {
+      float v[8];
+      gen_chunk(desc, a.basis, a.d, N, xr, XW, v);
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      *reinterpret_cast<uint4*>(phik + r * 128 + ((qd ^ (r & 7)) << 4)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    };
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
       ok = wait_bar(ptx::smem_addr(x_full), it & 1, abort_flag, a.status);
@@ -310,19 +426,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           if (!ok) break;
         }
         uint8_t* phik = phi + (size_t)kb * BN * 128;
-        for (int task = bt; task < BN * 8; task += kBasisThreads) {
-          const int r = task % BN, qd = task / BN;
-          const float* xr = xs + (r >> 7) * N * XW + (r % XW);
-          float v[8];
-          basis_run<8>(a.basis, a.d, a.Kp, xr, XW, kb * 64 + qd * 8, v);
-          uint32_t w[4];
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
-            w[h] = *reinterpret_cast<const uint32_t*>(&b2);
-          }
-          *reinterpret_cast<uint4*>(phik + r * 128 + ((qd ^ (r & 7)) << 4)) =
-              make_uint4(w[0], w[1], w[2], w[3]);
+        for (int qd = q0; qd < 8; qd += QS) {
+          const uint32_t desc = tab[kb * 8 + qd];
+          emit(phik, desc, qd, r0, xrow0);
+          if (R == 2) emit(phik, desc, qd, r0 + 128, xrow1);
         }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));
@@ -348,16 +455,18 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms) {
   pl.C = ceil_div(P, 128);
   pl.ok = false;
   const int cands[4] = {256, 128, 64, 32};
-  for (int i = 0; i < 4; ++i) {
-    const int BN = cands[i];
-    const int sm = smem_total(pl.KB, BN, s.N);
-    if (sm <= kMaxSmem) {
-      pl.BN = BN;
-      // at least half an SM's shared memory: one CTA per SM, so the tensor
-      // memory allocation never waits on a co-resident CTA
-      pl.smem_bytes = sm < kMinSmem ? kMinSmem : sm;
-      pl.ok = true;
-      break;
+  for (int i = 0; i < 4 && !pl.ok; ++i) {
+    for (int stages = 4; stages >= 3; --stages) {
+      const int sm = smem_plan(pl.KB, cands[i], s.N, stages).total;
+      if (sm <= kMaxSmem) {
+        pl.BN = cands[i];
+        pl.stages = stages;
+        // at least half an SM's shared memory: one CTA per SM, so the tensor
+        // memory allocation never waits on a co-resident CTA
+        pl.smem_bytes = sm < kMinSmem ? kMinSmem : sm;
+        pl.ok = true;
+        break;
+      }
     }
   }
   if (!pl.ok) return pl;
@@ -366,7 +475,7 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms) {
   int cols = 32;
   while (cols < 2 * pl.BN) cols <<= 1;
   pl.tmem_cols = cols;
-  pl.rows = pl.grid;
+  pl.rows = 2 * pl.grid;   // one partial row per (CTA, column half)
   return pl;
 }
 
@@ -384,6 +493,7 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.BN = pl.BN;
   a.KB = pl.KB;
   a.C = pl.C;
+  a.stages = pl.stages;
   const int last_cols = s.Kp - 64 * (pl.KB - 1);
   a.nmma_last = (last_cols + 15) / 16;
   a.ntiles = (int)(s.Mpad / pl.BN);

@@ -57,7 +57,7 @@ cudaError_t launch_fitness_fp32(const Fp32Plan& pl, const Shape& s, const float*
                                 const float* y, const float* popT, const float* a0, int P,
                                 int Ppad, double* part, cudaStream_t st);
 // fitness_tc.cu
-struct TcPlan { int BN, KB, C, grid, smem_bytes, tmem_cols, rows; bool ok; };
+struct TcPlan { int BN, KB, NS, C, stages, grid, smem_bytes, tmem_cols, rows; bool ok; };
 TcPlan plan_tc(const Shape& s, int P, int num_sms);
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0, int P,

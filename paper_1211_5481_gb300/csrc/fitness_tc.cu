@@ -416,6 +416,53 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       *reinterpret_cast<uint4*>(phik + r * 128 + ((qd ^ (r & 7)) << 4)) =
           make_uint4(w[0], w[1], w[2], w[3]);
     };
+    // both rows of a Chebyshev chunk that stays in one feature's run of
+    // degrees (the common case: degree 8): two interleaved recurrences, one
+    // descriptor decode, no per-value branches
+    auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
+      const int i = (int)(desc & 0xFFFFu);
+      const int j0 = (int)((desc >> 16) & 31u);
+      const float xa = xrow0[i * XW];
+      const float xb = R == 2 ? xrow1[i * XW] : 0.f;
+      const float a2 = xa + xa, b2 = xb + xb;
+      float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
+      for (int st = 1; st < j0; ++st) {
+        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+        tam = ta;
+        ta = na;
+        tbm = tb;
+        tb = nb;
+      }
+      float va[8], vb[8];
+      va[0] = ta;
+      vb[0] = tb;
+#pragma unroll
+      for (int e = 1; e < 8; ++e) {
+        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+        tam = ta;
+        ta = na;
+        tbm = tb;
+        tb = nb;
+        va[e] = ta;
+        vb[e] = tb;
+      }
+      uint32_t wa[4], wb[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 pa = __floats2bfloat162_rn(va[2 * h], va[2 * h + 1]);
+        const __nv_bfloat162 pb = __floats2bfloat162_rn(vb[2 * h], vb[2 * h + 1]);
+        wa[h] = *reinterpret_cast<const uint32_t*>(&pa);
+        wb[h] = *reinterpret_cast<const uint32_t*>(&pb);
+      }
+      *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
+          make_uint4(wa[0], wa[1], wa[2], wa[3]);
+      if (R == 2) {
+        const int r1 = r0 + 128;
+        *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
+            make_uint4(wb[0], wb[1], wb[2], wb[3]);
+      }
+    };
+    const bool cheb = a.basis == GAME_BASIS_CHEB;
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
       ok = wait_bar(ptx::smem_addr(x_full), it & 1, abort_flag, a.status);
@@ -428,8 +475,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         uint8_t* phik = phi + (size_t)kb * BN * 128;
         for (int qd = q0; qd < 8; qd += QS) {
           const uint32_t desc = tab[kb * 8 + qd];
-          emit(phik, desc, qd, r0, xrow0);
-          if (R == 2) emit(phik, desc, qd, r0 + 128, xrow1);
+          if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
+            emit_cheb_run2(phik, desc, qd);
+          } else {
+            emit(phik, desc, qd, r0, xrow0);
+            if (R == 2) emit(phik, desc, qd, r0 + 128, xrow1);
+          }
         }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));

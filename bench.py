@@ -50,6 +50,12 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes per launch of the dominant kernel, read + write, from the ncu
+# capture summarised in profiles/fitness_tc_M1000000_N32_cheb8_P1024_ncu.md
+# (valid for that kernel version and workload only; None elsewhere)
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.77e6 + 2.96e6}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -240,7 +246,8 @@ def main():
     if prec == game.GAME_PREC_BF16:
         peak = float(peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak, "traffic": None,
+                "frac": achieved_tflops / peak, "traffic": NCU_TRAFFIC.get((pr.name, args.form)),
+                "algorithmic_bytes": 4.0 * M * pr.N + 4.0 * M + 2.0 * P * (K - 1),
                 "peak_source": f"{peak_src} bf16_tflops (burst)",
                 "frac_of_sustained": achieved_tflops / float(peaks.get("bf16_tflops_sustained",
                                                                         peak)),

@@ -8,7 +8,8 @@ genes), P = 1024 chromosomes, sign targets with 5% flips; seeded synthetic
 data generated on the host and uploaded before timing. One step is one
 generation: selection / crossover / mutation kernels, the population pack,
 the fused fitness contraction (tensor cores, BF16 operands, FP32
-accumulation) and the FP64 cross-tile error sum. The plain FP32 CUDA-core
+accumulation), the FP64 cross-tile error sum and the re-scoring of the 8 best
+candidates (FP32 products, FP64 sums) before the next elitism decision. The plain FP32 CUDA-core
 form of the same step is timed beside it, and a sample of chromosomes is
 re-scored by the FP64 oracle to state the accuracy of both.
 
@@ -312,7 +313,7 @@ def main():
         cpu, _ = oracle_sample_rate(pr, 16)
 
     n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
-        2 * tm["operators_launches"]
+        2 * tm["operators_launches"] + 2 * tm["rescore_launches"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
@@ -320,14 +321,17 @@ def main():
         "data": "synthetic",
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "basis": "chebyshev", "contraction": args.form,
-                   "step": "one generation: operators + pack + fused fitness + FP64 reduce",
+                   "step": ("one generation: operators + pack + fused fitness + FP64 reduce"
+                            + (" + elite re-score (8 best: FP32 products, FP64 sums)"
+                               if prec == game.GAME_PREC_BF16 else "")),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},
         "generations_per_s": 1e3 / t_step,
         "vs_fp32": (value / fp32_leg["value"]) if fp32_leg else None,
         "fp32_form": fp32_leg,
         "stage_ms_per_step": {k.replace("_ms", ""): tm[k] / max(args.steps, 1)
-                              for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms")},
+                              for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms",
+                                        "rescore_ms")},
         "accuracy": acc,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -71,10 +71,15 @@ typedef struct {
   float reserved_f;
   double mse_threshold; /* game_train stops once best fitness < this; <= 0 off */
   uint64_t seed;        /* key of the counter-based generator (Philox4x32-10) */
-  int32_t reserved[8];  /* must be zero */
+  int32_t rescore_top;  /* 0..16: after every evaluation of the GA population
+                           in a reduced-precision form (not GAME_PREC_FP32),
+                           the rescore_top best chromosomes are re-scored as
+                           game_rescore_top does, before the operators rank
+                           them; 0 = off */
+  int32_t reserved[7];  /* must be zero */
 } game_params;
 
-/* Fills *out with the defaults listed above. */
+/* Fills *out with the defaults listed above (and rescore_top = 8). */
 int game_params_default(game_params* out);
 
 /* Creates a handle for one training set and copies it to the device.
@@ -105,6 +110,22 @@ int game_eval_fitness(game_t h, const float* pop, int32_t P, double* fit_out);
  * (GAME_PREC_*). */
 int game_eval_fitness_prec(game_t h, const float* pop, int32_t P,
                            int32_t precision, double* fit_out);
+
+/* Elite re-scoring. The n best chromosomes of fit (by fitness, then lower
+ * index; NaN ranks last) are evaluated again, and their entries of fit are
+ * replaced: the expansion of Eq. 1 / Eq. 6 and the gene sums of Eq. 2 in FP32
+ * (the arithmetic of GAME_PREC_FP32, relative error ~1e-7), the squared
+ * residuals of Eq. 3 summed in FP64. Its purpose is the elitism decision of
+ * Section 3 (2 elites, Section 5) when fit came from a reduced-precision
+ * contraction: the best candidates are then ranked by accurate values.
+ *   pop [P][K] FP32, fit [P] FP64 (in: any fitness vector of pop; out: the
+ *   same with n entries replaced), both host or both device;
+ *   1 <= n <= min(16, P); idx_out [n] (may be NULL; host or device) receives
+ *   the candidates' indices, best first.
+ * Entries other than the n candidates are not modified. Host arguments
+ * synchronise; device arguments only enqueue. */
+int game_rescore_top(game_t h, const float* pop, int32_t P, double* fit,
+                     int32_t n, int32_t* idx_out);
 
 /* One generation g -> g+1 of the GA state: elitism, tournament selection,
  * one-point crossover, per-gene Gaussian mutation, clamping to [-1, 1]
@@ -143,7 +164,9 @@ typedef struct {
   int64_t fitness_launches;
   int64_t pack_launches;
   int64_t reduce_launches;
-  int64_t operators_launches;
+  int64_t operators_launches; /* calls; two kernels each */
+  double rescore_ms;        /* elite candidate selection and re-scoring */
+  int64_t rescore_launches; /* calls; two kernels each */
 } game_timing;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */

@@ -89,6 +89,8 @@ def _load():
                                           u64, u32, vp]
         lib.oracle_train.argtypes = [vp, vp, i64, i32, i32, i32, i32,
                                      ctypes.POINTER(GAParams), u64, i32, i32, vp, vp, vp]
+        lib.oracle_select_best.argtypes = [vp, i32, i32, vp]
+        lib.oracle_rescore.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp, i32, vp, vp]
         lib.oracle_set_threads.argtypes = [i32]
         _lib = lib
     return _lib
@@ -206,6 +208,28 @@ def generation(pop, fit, seed, g, prm=None):
     _check(_load().oracle_generation(_ptr(pop), _ptr(fit), P, K, ctypes.byref(prm),
                                      seed, g, _ptr(nxt)), "generation")
     return nxt
+
+
+def select_best(fit, n):
+    """Indices of the n best by (fitness, index), NaN last, best first."""
+    fit = _f64(fit)
+    idx = np.zeros(n, dtype=np.int32)
+    _check(_load().oracle_select_best(_ptr(fit), fit.shape[0], n, _ptr(idx)), "select_best")
+    return idx
+
+
+def rescore(X, y, pop, d, basis, fit, n):
+    """fit with its n best entries replaced by their FP64 fitness; returns
+    (new fit, candidate indices best first)."""
+    X, y, fit = _f64(X), _f64(y), _f64(fit)
+    pop = np.ascontiguousarray(pop, dtype=np.float32)
+    M, N = X.shape
+    P = pop.shape[0]
+    out = np.zeros(P, dtype=np.float64)
+    idx = np.zeros(n, dtype=np.int32)
+    _check(_load().oracle_rescore(_ptr(X), _ptr(y), M, N, d, basis, _ptr(pop), P, _ptr(fit),
+                                  n, _ptr(out), _ptr(idx)), "rescore")
+    return out, idx
 
 
 def train(X, y, d, basis, P, G, seed, prm=None, use_gram=False):

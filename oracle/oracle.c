@@ -375,6 +375,40 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
   return 0;
 }
 
+int oracle_select_best(const double* fit, int32_t P, int32_t n, int32_t* idx) {
+  if (!fit || !idx || P < 1 || n < 0 || n > P) return -1;
+  unsigned char* taken = (unsigned char*)calloc((size_t)P, 1);
+  if (!taken) return -2;
+  for (int32_t r = 0; r < n; ++r) {
+    int32_t best = -1;
+    for (int32_t p = 0; p < P; ++p)
+      if (!taken[p] && (best < 0 || better(fit[p], p, fit[best], best))) best = p;
+    taken[best] = 1;
+    idx[r] = best;
+  }
+  free(taken);
+  return 0;
+}
+
+int oracle_rescore(const double* X, const double* y, int64_t M, int32_t N,
+                   int32_t d, int32_t basis, const float* pop, int32_t P,
+                   const double* fit_in, int32_t n, double* fit_out,
+                   int32_t* idx) {
+  const int64_t K = oracle_num_genes(N, d, basis);
+  if (K < 1 || !pop || !fit_in || !fit_out || !idx) return -1;
+  int rc = oracle_select_best(fit_in, P, n, idx);
+  if (rc) return rc;
+  memcpy(fit_out, fit_in, sizeof(double) * P);
+  double* a = (double*)malloc(sizeof(double) * K);
+  if (!a) return -2;
+  for (int32_t r = 0; r < n && !rc; ++r) {
+    for (int64_t k = 0; k < K; ++k) a[k] = (double)pop[(int64_t)idx[r] * K + k];
+    rc = oracle_fitness(X, y, M, N, d, basis, a, 1, &fit_out[idx[r]]);
+  }
+  free(a);
+  return rc;
+}
+
 int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
                  int32_t d, int32_t basis, int32_t P,
                  const oracle_ga_params* prm, uint64_t seed, int32_t G,

@@ -96,6 +96,19 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
                       int32_t K, const oracle_ga_params* prm, uint64_t seed,
                       uint32_t g, float* next);
 
+/* The n best chromosomes by (fitness, index), NaN ranking as +infinity:
+ * idx[0..n-1], best first (the ranking elitism uses, Section 3). */
+int oracle_select_best(const double* fit, int32_t P, int32_t n, int32_t* idx);
+
+/* Elite re-scoring: fit_out = fit_in with the entries of the n best (by
+ * oracle_select_best on fit_in) replaced by their FP64 fitness (the direct
+ * form of oracle_fitness). idx[n] receives the candidates, best first.
+ * pop[P][K] FP32 genes. */
+int oracle_rescore(const double* X, const double* y, int64_t M, int32_t N,
+                   int32_t d, int32_t basis, const float* pop, int32_t P,
+                   const double* fit_in, int32_t n, double* fit_out,
+                   int32_t* idx);
+
 /* Whole GA run: init, then G times (fitness, generation), with the fitness
  * computed by the direct form (use_gram = 0) or the Gram form (1).
  * best[G+1] receives the best fitness after init and after each generation.

@@ -81,6 +81,11 @@ struct game_ctx {
   int64_t gen = 0;
   int4* plan = nullptr;
   int* status = nullptr;   // device status word written by kernels
+  // elite re-scoring
+  int* cand = nullptr;
+  RescorePlan rplan{};
+  double* rpart = nullptr;
+  unsigned int* tickets = nullptr;
   // evaluation scratch, grown on demand
   int cap_P = 0;
   float* popT = nullptr;
@@ -99,13 +104,13 @@ struct game_ctx {
     int kind;
   };
   std::vector<Span> spans;
-  double tot_ms[4] = {0, 0, 0, 0};
-  int64_t count[4] = {0, 0, 0, 0};
+  double tot_ms[5] = {0, 0, 0, 0, 0};
+  int64_t count[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
 
-enum StageKind { kFitness = 0, kPack = 1, kReduce = 2, kOperators = 3 };
+enum StageKind { kFitness = 0, kPack = 1, kReduce = 2, kOperators = 3, kRescore = 4 };
 
 // Records the start event of a timed stage (no-op when timing is off).
 cudaEvent_t stage_begin(game_ctx* h) {
@@ -221,6 +226,27 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
   return GAME_OK;
 }
 
+// Enqueues the re-scoring of the n best entries of dfit (device arrays).
+int rescore_device(game_ctx* h, const float* dpop, int P, int n, double* dfit) {
+  cudaEvent_t t0 = stage_begin(h);
+  CK(launch_rescore(h->rplan, h->s, h->Xt, h->y, dpop, P, n, dfit, h->cand, h->rpart,
+                    h->tickets, h->st));
+  stage_end(h, t0, kRescore);
+  return GAME_OK;
+}
+
+// Fitness of the GA population: the contraction in the handle's precision,
+// then, for the reduced-precision forms, the re-scoring of the best
+// candidates before the operators rank them.
+int eval_state(game_ctx* h) {
+  int rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+  if (rc) return rc;
+  const int n = h->prm.rescore_top < h->prm.P ? h->prm.rescore_top : h->prm.P;
+  if (h->prm.precision != GAME_PREC_FP32 && n > 0)
+    return rescore_device(h, h->pop[h->cur], h->prm.P, n, h->fit);
+  return GAME_OK;
+}
+
 int check_status(game_ctx* h) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -268,6 +294,10 @@ int validate_params(const game_params& p, const Shape& s, std::string* why) {
     *why = "unknown precision";
     return 0;
   }
+  if (p.rescore_top < 0 || p.rescore_top > kMaxRescore) {
+    *why = "rescore_top must be in 0..16";
+    return 0;
+  }
   if (p.check_every < 0) {
     *why = "check_every must be >= 0";
     return 0;
@@ -299,6 +329,9 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->fit);
   dev_free(h->plan);
   dev_free(h->status);
+  dev_free(h->cand);
+  dev_free(h->rpart);
+  dev_free(h->tickets);
   dev_free(h->popT);
   dev_free(h->popA);
   dev_free(h->a0);
@@ -333,6 +366,7 @@ int game_params_default(game_params* out) {
   out->sigma = 0.1f;
   out->mse_threshold = 0.0;
   out->seed = 1;
+  out->rescore_top = 8;
   return GAME_OK;
 }
 
@@ -380,13 +414,17 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) return bail(cuda_fail(e, "multiprocessor count"));
 
+  h->rplan = plan_rescore(s, h->num_sms);
   if (dev_alloc(&h->Xt, (size_t)s.Mpad * N) != cudaSuccess ||
       dev_alloc(&h->y, (size_t)s.Mpad) != cudaSuccess ||
       dev_alloc(&h->pop[0], (size_t)p.P * s.K) != cudaSuccess ||
       dev_alloc(&h->pop[1], (size_t)p.P * s.K) != cudaSuccess ||
       dev_alloc(&h->fit, (size_t)p.P) != cudaSuccess ||
       dev_alloc(&h->plan, (size_t)p.P) != cudaSuccess ||
-      dev_alloc(&h->status, 4) != cudaSuccess) {
+      dev_alloc(&h->status, 4) != cudaSuccess ||
+      dev_alloc(&h->cand, kMaxRescore) != cudaSuccess ||
+      dev_alloc(&h->rpart, (size_t)2 * h->rplan.grid * 8) != cudaSuccess ||
+      dev_alloc(&h->tickets, 2) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(GAME_ENOMEM, "device allocation of the training set / GA state"));
   }
@@ -410,6 +448,7 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
     dy = tmpy;
   }
   int bad_h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->tickets, 0, 2 * sizeof(unsigned int), h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
   if (e == cudaSuccess) e = launch_relayout_X(dX, dy, s, h->Xt, h->y, h->status, h->st);
   if (e == cudaSuccess)
@@ -425,7 +464,7 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   // generation 0: uniform genes, then their fitness
   e = launch_init_population(p.seed, p.P, s.K, h->pop[0], h->st);
   if (e != cudaSuccess) return bail(cuda_fail(e, "init population"));
-  rc = eval_device(h, h->pop[0], p.P, p.precision, h->fit);
+  rc = eval_state(h);
   if (rc) return bail(rc);
   rc = check_status(h);
   if (rc) return bail(rc);
@@ -480,13 +519,52 @@ int game_eval_fitness(game_t h, const float* pop, int32_t P, double* fit_out) {
   return game_eval_fitness_prec(h, pop, P, h->prm.precision, fit_out);
 }
 
+int game_rescore_top(game_t h, const float* pop, int32_t P, double* fit, int32_t n,
+                     int32_t* idx_out) {
+  g_last_error.clear();
+  if (!h || !pop || !fit) return fail(GAME_EINVAL, "NULL argument");
+  if (P < 1 || P > (1 << 24)) return fail(GAME_EINVAL, "P must be in 1..2^24");
+  if (n < 1 || n > kMaxRescore || n > P) return fail(GAME_EINVAL, "n must be in 1..min(16, P)");
+  const bool dev_in = is_device_ptr(pop), dev_fit = is_device_ptr(fit);
+  if (dev_in != dev_fit) return fail(GAME_EINVAL, "pop and fit must be in the same memory");
+  int rc;
+  if (dev_in) {
+    rc = rescore_device(h, pop, P, n, fit);
+  } else {
+    if (P > h->ucap) {
+      dev_free(h->upop);
+      dev_free(h->ufit);
+      h->upop = nullptr;
+      h->ufit = nullptr;
+      h->ucap = 0;
+      if (dev_alloc(&h->upop, (size_t)P * h->s.K) != cudaSuccess ||
+          dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "device copy of the population");
+      }
+      h->ucap = P;
+    }
+    CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->s.K * sizeof(float),
+                       cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->ufit, fit, (size_t)P * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    rc = rescore_device(h, h->upop, P, n, h->ufit);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(fit, h->ufit, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  }
+  if (rc) return rc;
+  if (idx_out)
+    CK(cudaMemcpyAsync(idx_out, h->cand, (size_t)n * sizeof(int32_t), cudaMemcpyDefault, h->st));
+  if (!dev_in || (idx_out && !is_device_ptr(idx_out))) return check_status(h);
+  return GAME_OK;
+}
+
 int game_generation(game_t h, uint64_t seed) {
   g_last_error.clear();
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   if (h->gen >= 0xFFFFFFFFll) return fail(GAME_ESTATE, "generation counter exhausted");
   int rc;
   if (!h->fit_valid) {
-    rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+    rc = eval_state(h);
     if (rc) return rc;
     h->fit_valid = true;
   }
@@ -497,7 +575,7 @@ int game_generation(game_t h, uint64_t seed) {
   h->cur ^= 1;
   h->gen += 1;
   h->fit_valid = false;
-  rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+  rc = eval_state(h);
   if (rc) return rc;
   h->fit_valid = true;
   return GAME_OK;
@@ -552,7 +630,7 @@ int game_get_population(game_t h, float* pop_out, double* fit_out, int64_t* gene
   }
   if (fit_out) {
     if (!h->fit_valid) {
-      int rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+      int rc = eval_state(h);
       if (rc) return rc;
       h->fit_valid = true;
     }
@@ -574,7 +652,7 @@ int game_set_state(game_t h, const float* pop, const double* fit, int64_t genera
     rc = copy_in(h, h->fit, fit, (size_t)h->prm.P * sizeof(double));
     if (rc) return rc;
   } else {
-    rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
+    rc = eval_state(h);
     if (rc) return rc;
   }
   h->fit_valid = true;
@@ -585,7 +663,7 @@ int game_set_state(game_t h, const float* pop, const double* fit, int64_t genera
 int game_set_timing(game_t h, int32_t enable) {
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   harvest_spans(h);
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     h->tot_ms[k] = 0.0;
     h->count[k] = 0;
   }
@@ -604,6 +682,8 @@ int game_get_timing(game_t h, game_timing* out) {
   out->pack_launches = h->count[kPack];
   out->reduce_launches = h->count[kReduce];
   out->operators_launches = h->count[kOperators];
+  out->rescore_ms = h->tot_ms[kRescore];
+  out->rescore_launches = h->count[kRescore];
   return GAME_OK;
 }
 

@@ -17,6 +17,10 @@
 //                                 shared memory.
 //   a0   [Ppad] FP32              bias genes.
 //   part [rows][Ppad] FP64        per-CTA partial sums of squared residuals.
+// Elite re-scoring (fixed size, allocated with the handle):
+//   cand [16] int32               candidate indices, best first.
+//   rpart [2][grid][8] FP64       per-CTA partial sums of the re-scored candidates.
+//   tickets [2] uint32            finish counters of the re-scoring CTAs (self-resetting).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -29,6 +33,7 @@ namespace game {
 constexpr int kPatBlock = 128;   // patterns per stored X block
 constexpr int kMaxK = 4097;      // genes per chromosome accepted
 constexpr int kMaxTournament = 64;
+constexpr int kMaxRescore = 16;  // elite candidates re-scored at most
 
 // Status word written by kernels (0 = fine).
 enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevBadShape = 2 };
@@ -62,6 +67,13 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms);
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0, int P,
                               int Ppad, double* part, int* status, cudaStream_t st);
+// rescore.cu
+struct RescorePlan { int pt, grid; };   // patterns per thread, CTAs per candidate group
+RescorePlan plan_rescore(const Shape& s, int num_sms);
+size_t rescore_smem_bytes(const Shape& s);
+cudaError_t launch_rescore(const RescorePlan& pl, const Shape& s, const float* Xt,
+                           const float* y, const float* pop, int P, int n, double* fit,
+                           int* cand, double* part, unsigned int* tickets, cudaStream_t st);
 // api.cu
 void record_error(const char* msg);
 // reduce.cu

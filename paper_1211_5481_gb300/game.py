@@ -34,7 +34,7 @@ _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA
 EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_fitness",
             "game_eval_fitness_prec", "game_generation", "game_train", "game_get_population",
             "game_set_state", "game_set_timing", "game_get_timing", "game_sync",
-            "game_destroy", "game_last_error", "game_eval_fitness_static")
+            "game_destroy", "game_last_error", "game_eval_fitness_static", "game_rescore_top")
 
 
 class GameError(RuntimeError):
@@ -57,7 +57,8 @@ class game_params(ctypes.Structure):
         ("reserved_f", ctypes.c_float),
         ("mse_threshold", ctypes.c_double),
         ("seed", ctypes.c_uint64),
-        ("reserved", ctypes.c_int32 * 8),
+        ("rescore_top", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -71,6 +72,8 @@ class game_timing(ctypes.Structure):
         ("pack_launches", ctypes.c_int64),
         ("reduce_launches", ctypes.c_int64),
         ("operators_launches", ctypes.c_int64),
+        ("rescore_ms", ctypes.c_double),
+        ("rescore_launches", ctypes.c_int64),
     ]
 
 
@@ -110,6 +113,7 @@ def load(build_if_missing: bool = True):
         "game_sync": [vp],
         "game_destroy": [vp],
         "game_eval_fitness_static": [vp, vp, i64, i32, i32, i32, vp, i32, dp, vp],
+        "game_rescore_top": [vp, vp, i32, dp, i32, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -178,6 +182,13 @@ def game_eval_fitness(h, pop, fit_out, precision: int | None = None):
     return fit_out
 
 
+def game_rescore_top(h, pop, fit, n: int, idx_out=None):
+    """pop [P][K] float32, fit [P] float64 (updated in place), idx_out [n] int32;
+    numpy arrays or CUDA tensors (pop and fit in the same memory)."""
+    _check(load().game_rescore_top(h, _ptr(pop), pop.shape[0], _ptr(fit), n, _ptr(idx_out)))
+    return fit
+
+
 def game_generation(h, seed: int):
     _check(load().game_generation(h, seed))
 
@@ -244,6 +255,19 @@ class Game:
             import torch
             fit = torch.empty(pop.shape[0], dtype=torch.float64, device=pop.device)
         return game_eval_fitness(self.h, pop, fit, precision)
+
+    def rescore_top(self, pop, fit, n):
+        """Returns (fit with the n best re-scored, their indices best first)."""
+        if isinstance(pop, np.ndarray):
+            pop = np.ascontiguousarray(pop, dtype=np.float32)
+            fit = np.array(fit, dtype=np.float64)
+            idx = np.zeros(n, dtype=np.int32)
+        else:
+            import torch
+            fit = fit.clone()
+            idx = torch.empty(n, dtype=torch.int32, device=pop.device)
+        game_rescore_top(self.h, pop, fit, n, idx)
+        return fit, idx
 
     def generation(self, seed):
         game_generation(self.h, seed)

@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--M", type=int, default=1_000_000, help="patterns (smaller for profiling)")
-    ap.add_argument("--form", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--form", choices=["bf16", "bf16x3", "fp8", "fp32"], default="bf16")
     ap.add_argument("--no-fp32-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -200,7 +200,9 @@ def main():
     Xd = torch.from_numpy(pr.X).to(dev)
     yd = torch.from_numpy(pr.y).to(dev)
     game.load()
-    prec = game.GAME_PREC_BF16 if args.form == "bf16" else game.GAME_PREC_FP32
+    prec = {"fp32": game.GAME_PREC_FP32, "bf16": game.GAME_PREC_BF16,
+            "bf16x3": game.GAME_PREC_BF16X3, "fp8": game.GAME_PREC_FP8}[args.form]
+    tensor = prec != game.GAME_PREC_FP32
     g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -244,14 +246,20 @@ def main():
     flops_launch = 2.0 * M * P * (K - 1) + 3.0 * M * P
     fit_ms = tm["fitness_ms"] / max(tm["fitness_launches"], 1)
     achieved_tflops = flops_launch / (fit_ms * 1e-3) / 1e12
-    if prec == game.GAME_PREC_BF16:
-        peak = float(peaks["bf16_tflops"])
+    if tensor:
+        # FP8 runs at twice the BF16 rate (nominal 4.5 vs 2.25 PFLOP/s dense);
+        # bf16x3 issues three BF16 MMAs per useful product
+        ratio = 2.0 if prec == game.GAME_PREC_FP8 else 1.0
+        mma_per_product = 3.0 if prec == game.GAME_PREC_BF16X3 else 1.0
+        peak = float(peaks["bf16_tflops"]) * ratio
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak, "traffic": NCU_TRAFFIC.get((pr.name, args.form)),
                 "algorithmic_bytes": 4.0 * M * pr.N + 4.0 * M + 2.0 * P * (K - 1),
-                "peak_source": f"{peak_src} bf16_tflops (burst)",
-                "frac_of_sustained": achieved_tflops / float(peaks.get("bf16_tflops_sustained",
-                                                                        peak)),
+                "peak_source": (f"{peak_src} bf16_tflops (burst)"
+                                + (" x 2 (FP8 / BF16 nominal ratio)" if ratio != 1.0 else "")),
+                "frac_of_sustained": achieved_tflops / (float(peaks.get(
+                    "bf16_tflops_sustained", peaks["bf16_tflops"])) * ratio),
+                "mma_tflops": achieved_tflops * mma_per_product,
                 "kernel": "fitness_tc_kernel", "kernel_ms": fit_ms}
     else:
         props = torch.cuda.get_device_properties(dev)
@@ -263,7 +271,7 @@ def main():
 
     # plain FP32 GPU form of the same step, for the "vs plain FP32" ratio
     fp32_leg = None
-    if prec == game.GAME_PREC_BF16 and not args.no_fp32_leg:
+    if tensor and not args.no_fp32_leg:
         g32 = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P,
                         precision=game.GAME_PREC_FP32, seed=2)
         ms32, tm32 = timed_steps(g32, max(3, args.steps // 4), 3)
@@ -303,12 +311,12 @@ def main():
         pop_np, fit_np, gen = g.population()
         sample = np.linspace(0, P - 1, 8).astype(int)
         ref = oracle.fitness(pr.X, pr.y, pop_np[sample], pr.degree, pr.basis)
-        f_bf = g.eval_fitness(pop_np, precision=game.GAME_PREC_BF16)
+        f_bf = g.eval_fitness(pop_np, precision=prec)
         f_32 = g.eval_fitness(pop_np, precision=game.GAME_PREC_FP32)
         acc = {"sample_chromosomes": len(sample), "generation": gen,
-               "bf16_max_rel_err": float(np.max(np.abs(f_bf[sample] - ref) / ref)),
+               "form_max_rel_err": float(np.max(np.abs(f_bf[sample] - ref) / ref)),
                "fp32_max_rel_err": float(np.max(np.abs(f_32[sample] - ref) / ref)),
-               "top10_agreement_bf16_vs_fp32": len(set(np.argsort(f_bf)[:10]) &
+               "top10_agreement_form_vs_fp32": len(set(np.argsort(f_bf)[:10]) &
                                                     set(np.argsort(f_32)[:10])) / 10}
         cpu, _ = oracle_sample_rate(pr, 16)
 
@@ -317,13 +325,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3",
+                                               "fp8": "e4m3"}[args.form],
         "data": "synthetic",
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "basis": "chebyshev", "contraction": args.form,
                    "step": ("one generation: operators + pack + fused fitness + FP64 reduce"
                             + (" + elite re-score (8 best: FP32 products, FP64 sums)"
-                               if prec == game.GAME_PREC_BF16 else "")),
+                               if tensor else "")),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},
         "generations_per_s": 1e3 / t_step,

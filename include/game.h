@@ -47,9 +47,21 @@ extern "C" {
 #define GAME_BASIS_CHEB 0
 #define GAME_BASIS_TRIG 1
 
-/* Arithmetic of the fitness contraction (the expansion-times-genes sum). */
+/* Arithmetic of the fitness contraction (the expansion-times-genes sum). In
+ * every form the residuals of Eq. 3 are squared in FP32 and the sum over
+ * patterns ends in FP64. */
 #define GAME_PREC_FP32 0   /* FP32 CUDA-core FFMA, FP32 accumulation */
 #define GAME_PREC_BF16 1   /* tcgen05 BF16 x BF16 -> FP32 in tensor memory */
+#define GAME_PREC_BF16X3 2 /* tcgen05 split products: genes and expansion split
+                              into BF16 hi + lo, three MMAs (hi*hi + hi*lo +
+                              lo*hi) into one FP32 accumulator; both split
+                              operands must fit in shared memory, which limits
+                              K - 1 to 1216 at N <= 64 (GAME_EINVAL beyond) */
+#define GAME_PREC_FP8 3    /* tcgen05 FP8 E4M3 x E4M3 -> FP32: expansion column
+                              k scaled by 448 / max_m |phi_k(x_m)| (taken once
+                              from the training set), genes by the inverse
+                              and a per-chromosome factor restored in the
+                              epilogue */
 
 typedef struct game_ctx* game_t;
 

@@ -91,7 +91,12 @@ struct game_ctx {
   float* popT = nullptr;
   uint8_t* popA = nullptr;
   float* a0 = nullptr;
+  float* uscale = nullptr;     // FP8: per-chromosome scales [cap_P]
   double* part = nullptr;
+  // FP8 column scales of the expansion (computed once, at the first FP8 use)
+  unsigned int* colmax = nullptr;
+  float* colscale = nullptr;
+  float* colinv = nullptr;
   size_t part_cap = 0;
   float* upop = nullptr;    // device copy of a host population
   double* ufit = nullptr;
@@ -147,12 +152,46 @@ void stage_end(game_ctx* h, cudaEvent_t start, int kind) {
   if (h->spans.size() > 8192) harvest_spans(h);
 }
 
+bool valid_precision(int prec) {
+  return prec == GAME_PREC_FP32 || prec == GAME_PREC_BF16 || prec == GAME_PREC_BF16X3 ||
+         prec == GAME_PREC_FP8;
+}
+
+// tensor-core operand form of a reduced-precision GAME_PREC_*
+int tc_form(int prec) {
+  return prec == GAME_PREC_BF16X3 ? kFormBF16x3 : prec == GAME_PREC_FP8 ? kFormFP8 : kFormBF16;
+}
+
+// FP8 per-column scales of the training set's expansion, once per handle.
+int ensure_colscales(game_ctx* h) {
+  if (h->colinv) return GAME_OK;
+  const int ncols = ceil_div(h->s.Kp, 128) * 128;
+  if (dev_alloc(&h->colmax, ncols) != cudaSuccess || dev_alloc(&h->colscale, ncols) != cudaSuccess ||
+      dev_alloc(&h->colinv, ncols) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(h->colmax);
+    dev_free(h->colscale);
+    dev_free(h->colinv);
+    h->colmax = nullptr;
+    h->colscale = nullptr;
+    h->colinv = nullptr;
+    return fail(GAME_ENOMEM, "FP8 column scales");
+  }
+  CK(cudaMemsetAsync(h->colmax, 0, ncols * sizeof(unsigned int), h->st));
+  CK(launch_colmax(h->s, h->Xt, h->colmax, ncols, h->st));
+  CK(launch_colscales(h->colmax, ncols, h->colscale, h->colinv, h->st));
+  return GAME_OK;
+}
+
 int ensure_scratch(game_ctx* h, int P, int prec) {
   const int Ppad = ceil_div(P, 128) * 128;
   if (Ppad > h->cap_P) {
     dev_free(h->a0);
+    dev_free(h->uscale);
     h->a0 = nullptr;
-    if (dev_alloc(&h->a0, Ppad) != cudaSuccess) return fail(GAME_ENOMEM, "a0 allocation");
+    h->uscale = nullptr;
+    if (dev_alloc(&h->a0, Ppad) != cudaSuccess || dev_alloc(&h->uscale, Ppad) != cudaSuccess)
+      return fail(GAME_ENOMEM, "a0 allocation");
     h->cap_P = Ppad;
   }
   if (prec == GAME_PREC_FP32) {
@@ -172,10 +211,14 @@ int ensure_scratch(game_ctx* h, int P, int prec) {
       h->part_cap = pneed;
     }
   } else {
-    const TcPlan pl = plan_tc(h->s, P, h->num_sms);
+    const TcPlan pl = plan_tc(h->s, P, h->num_sms, tc_form(prec));
     if (!pl.ok)
       return fail(GAME_EINVAL, "contraction length too large for the tensor-core path");
-    const size_t need = (size_t)pl.C * pl.KB * 128 * 128;
+    if (pl.form == kFormFP8) {
+      const int rc = ensure_colscales(h);
+      if (rc) return rc;
+    }
+    const size_t need = (size_t)pl.C * pl.KB * form_na(pl.form) * 128 * 128;
     if (need > h->popA_cap) {
       dev_free(h->popA);
       h->popA = nullptr;
@@ -211,13 +254,14 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
     CK(launch_reduce(h->part, pl.grid_y, P, Ppad, h->s.M, dfit, h->st));
     stage_end(h, t0, kReduce);
   } else {
-    const TcPlan pl = plan_tc(h->s, P, h->num_sms);
+    const TcPlan pl = plan_tc(h->s, P, h->num_sms, tc_form(prec));
     t0 = stage_begin(h);
-    CK(launch_pack_bf16(dpop, P, pl.C, h->s, pl.KB, h->popA, h->a0, h->st));
+    CK(launch_pack_tc(pl.form, dpop, P, pl.C, h->s, pl.KB, h->colscale, h->popA, h->a0,
+                      h->uscale, h->st));
     stage_end(h, t0, kPack);
     t0 = stage_begin(h);
-    CK(launch_fitness_tc(pl, h->s, h->Xt, h->y, h->popA, h->a0, P, Ppad, h->part, h->status,
-                         h->st));
+    CK(launch_fitness_tc(pl, h->s, h->Xt, h->y, h->popA, h->a0, h->uscale, h->colinv, P, Ppad,
+                         h->part, h->status, h->st));
     stage_end(h, t0, kFitness);
     t0 = stage_begin(h);
     CK(launch_reduce(h->part, pl.rows, P, Ppad, h->s.M, dfit, h->st));
@@ -290,7 +334,7 @@ int validate_params(const game_params& p, const Shape& s, std::string* why) {
     *why = "sigma must be finite and >= 0";
     return 0;
   }
-  if (p.precision != GAME_PREC_FP32 && p.precision != GAME_PREC_BF16) {
+  if (!valid_precision(p.precision)) {
     *why = "unknown precision";
     return 0;
   }
@@ -335,6 +379,10 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->popT);
   dev_free(h->popA);
   dev_free(h->a0);
+  dev_free(h->uscale);
+  dev_free(h->colmax);
+  dev_free(h->colscale);
+  dev_free(h->colinv);
   dev_free(h->part);
   dev_free(h->upop);
   dev_free(h->ufit);
@@ -488,8 +536,7 @@ int game_eval_fitness_prec(game_t h, const float* pop, int32_t P, int32_t precis
   g_last_error.clear();
   if (!h || !pop || !fit_out) return fail(GAME_EINVAL, "NULL argument");
   if (P < 1 || P > (1 << 24)) return fail(GAME_EINVAL, "P must be in 1..2^24");
-  if (precision != GAME_PREC_FP32 && precision != GAME_PREC_BF16)
-    return fail(GAME_EINVAL, "unknown precision");
+  if (!valid_precision(precision)) return fail(GAME_EINVAL, "unknown precision");
   const bool dev_in = is_device_ptr(pop), dev_out = is_device_ptr(fit_out);
   if (dev_in != dev_out) return fail(GAME_EINVAL, "pop and fit_out must be in the same memory");
   if (dev_in) return eval_device(h, pop, P, precision, fit_out);

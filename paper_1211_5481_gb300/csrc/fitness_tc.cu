@@ -1,6 +1,18 @@
 // fitness_tc.cu -- fitness of a population with the contraction on the
-// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
-// tensor memory), the squared-error reduction fused into the epilogue.
+// 5th-generation tensor cores (tcgen05, FP32 accumulation in tensor memory),
+// the squared-error reduction fused into the epilogue.
+//
+// Operand forms (template parameter F):
+//   BF16      genes and expansion rounded to BF16, one kind::f16 MMA per K=16.
+//   bf16x3    split products: x = hi + lo with hi = bf16(x), lo = bf16(x - hi)
+//             for both operands, and per K=16 step three MMAs into the same
+//             accumulator, A_hi PHI_hi + A_hi PHI_lo + A_lo PHI_hi (the lo*lo
+//             term, below 2^-16 of the product, is dropped).
+//   FP8 E4M3  kind::f8f6f4, K = 32 per MMA, 128 columns per K-block. Column k
+//             of the expansion is scaled by colinv_k = 448 / max_m |phi_k| into
+//             E4M3's range; the genes carry colscale_k = 1 / colinv_k and a
+//             per-chromosome factor 1 / u_p (u_p = max_k |a_pk colscale_k| / 448),
+//             which the epilogue restores: Out = a_0 + u_p * D.
 //
 // Math (paper Section 3): Out_p(m) = a_{p,0} + sum_c a_{p,c+1} phi_c(x_m)
 // (Eq. 2), fit_p = (1/M) sum_m (y_m - Out_p(m))^2 (Eq. 3, MSE). The
@@ -36,6 +48,8 @@
 // PHI and D never leave the SM. All waits are bounded (2 s): on expiry the
 // kernel raises a status word, abandons its loops, waits for its own bulk
 // copies and MMAs in flight, frees tensor memory and returns.
+#include <cuda_fp8.h>
+
 #include "basis.cuh"
 #include "game_internal.cuh"
 #include "tc_ptx.cuh"
@@ -65,24 +79,27 @@ struct TcArgs {
   const float* y;
   const uint8_t* popA;
   const float* a0;
+  const float* uscale;   // FP8 only
+  const float* colinv;   // FP8 only, [KB * 128]
   double* part;
   int* status;
 };
 
 struct SmemPlan {
-  int phi, ast, xs, tab, bars, total;
+  int phi, ast, xs, cs, tab, bars, total;
 };
 
 __host__ __device__ inline int num_bars(int KB, int stages) { return 2 * stages + 2 * KB + 7; }
 
 // Byte offsets of the shared-memory regions from the 1024-aligned base.
-__host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages) {
+__host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages, int F) {
   SmemPlan s;
   s.phi = 0;
-  s.ast = s.phi + KB * BN * 128;
-  s.xs = s.ast + stages * (int)kABytes;
-  s.tab = s.xs + N * BN * 4;
-  s.bars = (s.tab + KB * 8 * 4 + 7) & ~7;
+  s.ast = s.phi + KB * form_nphi(F) * BN * 128;
+  s.xs = s.ast + stages * form_na(F) * (int)kABytes;
+  s.cs = s.xs + N * BN * 4;
+  s.tab = s.cs + (F == kFormFP8 ? KB * 128 * 4 : 0);
+  s.bars = (s.tab + KB * (form_cols(F) / 8) * 4 + 7) & ~7;
   s.total = s.bars + num_bars(KB, stages) * 8 + 16 + 1024;   // + alignment slack
   return s;
 }
@@ -117,32 +134,55 @@ __device__ void wait_bar_drain(uint32_t bar, uint32_t parity, int* status) {
   }
 }
 
-// sse += ((y - bias) - acc)^2 over 32 columns, two columns per packed op.
+// sse += ((y - bias) - u * acc)^2 over 32 columns, two columns per packed op
+// (u = 1 except for FP8, where -u * acc + (y - bias) is one rounding as
+// (y - bias) - acc is for u = 1).
 __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* yc,
-                                          uint64_t bias2, uint64_t& s2) {
+                                          uint64_t bias2, uint64_t negu2, uint64_t& s2) {
 #pragma unroll
   for (int e4 = 0; e4 < 8; ++e4) {
     const float4 yv = __ldg(reinterpret_cast<const float4*>(yc) + e4);
     const uint64_t ya = ptx::f2_sub(ptx::f2_pack(yv.x, yv.y), bias2);
     const uint64_t yb = ptx::f2_sub(ptx::f2_pack(yv.z, yv.w), bias2);
-    const uint64_t ra = ptx::f2_sub(ya, ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]),
-                                                     __uint_as_float(v[4 * e4 + 1])));
-    const uint64_t rb = ptx::f2_sub(yb, ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]),
-                                                     __uint_as_float(v[4 * e4 + 3])));
+    const uint64_t ra = ptx::f2_fma(negu2, ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]),
+                                                        __uint_as_float(v[4 * e4 + 1])), ya);
+    const uint64_t rb = ptx::f2_fma(negu2, ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]),
+                                                        __uint_as_float(v[4 * e4 + 3])), yb);
     s2 = ptx::f2_fma(ra, ra, s2);
     s2 = ptx::f2_fma(rb, rb, s2);
   }
 }
 
+// Rounds 2 x 8 values to BF16 pairs (hi), and for bf16x3 also the residuals
+// v - hi (lo).
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo_col, float hi_col) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+__device__ __forceinline__ void split_bf16x2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+  const float2 hf = __bfloat1622float2(h);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = bf16x2_bits(v0 - hf.x, v1 - hf.y);
+}
+__device__ __forceinline__ uint32_t e4m3x4_bits(float v0, float v1, float v2, float v3) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
+
+template <int F>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a) {
+  constexpr int NA = form_na(F), NPHI = form_nphi(F), CPK = form_cols(F) / 8;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int BN = a.BN, KB = a.KB, N = a.N, S = a.stages;
-  const SmemPlan sp = smem_plan(KB, BN, N, S);
+  const SmemPlan sp = smem_plan(KB, BN, N, S, F);
   uint8_t* phi = base + sp.phi;
   uint8_t* ast = base + sp.ast;
   float* xs = reinterpret_cast<float*>(base + sp.xs);
+  float* cs = reinterpret_cast<float*>(base + sp.cs);
   uint32_t* tab = reinterpret_cast<uint32_t*>(base + sp.tab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + sp.bars);
   uint64_t* a_full = bars;
@@ -201,9 +241,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int kb = 0; kb < KB && ok; ++kb) {
             ok = wait_bar(ptx::smem_addr(&a_empty[s]), ph ^ 1, abort_flag, a.status);
             if (!ok) break;
-            ptx::mbar_arrive_expect_tx(ptx::smem_addr(&a_full[s]), kABytes);
-            ptx::bulk_g2s(ptx::smem_addr(ast + s * kABytes),
-                          a.popA + (size_t)(c * KB + kb) * kABytes, kABytes,
+            ptx::mbar_arrive_expect_tx(ptx::smem_addr(&a_full[s]), NA * kABytes);
+            ptx::bulk_g2s(ptx::smem_addr(ast + s * NA * kABytes),
+                          a.popA + (size_t)(c * KB + kb) * NA * kABytes, NA * kABytes,
                           ptx::smem_addr(&a_full[s]));
             ++q;
             if (++s == (uint32_t)S) {
@@ -225,29 +265,44 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
     // taken in pairs (both operand waits first, then up to eight MMAs back
     // to back, then the commits), and the inner groups are unrolled.
     if (lane == 0) {
-      const uint32_t idesc = ptx::idesc_bf16_f32(128, BN);
+      const uint32_t idesc =
+          F == kFormFP8 ? ptx::idesc_e4m3_f32(128, BN) : ptx::idesc_bf16_f32(128, BN);
       const uint64_t adesc0 = ptx::desc_kmajor_sw128(ptx::smem_addr(ast));
       const uint64_t bdesc0 = ptx::desc_kmajor_sw128(ptx::smem_addr(phi));
-      const uint32_t a_step = kABytes >> 4;                  // one A stage
-      const uint32_t b_step = (uint32_t)(BN * 128) >> 4;     // one expansion K-block
+      const uint32_t a_step = (uint32_t)(NA * kABytes) >> 4;       // one A stage
+      const uint32_t b_step = (uint32_t)(NPHI * BN * 128) >> 4;    // one expansion K-block
+      const uint32_t a_lo = kABytes >> 4;                          // bf16x3: lo gene block
+      const uint32_t b_lo = (uint32_t)(BN * 128) >> 4;             // bf16x3: lo expansion
       const uint32_t a_full0 = ptx::smem_addr(a_full), a_empty0 = ptx::smem_addr(a_empty);
       const uint32_t phi_full0 = ptx::smem_addr(phi_full), phi_free0 = ptx::smem_addr(phi_free);
       const uint32_t acc_full0 = ptx::smem_addr(acc_full), acc_empty0 = ptx::smem_addr(acc_empty);
       const int nlast = a.nmma_last;
       uint32_t s = 0, ph = 0, acc_it = 0;   // A stage and its phase, accumulator count
       bool ok = true;
-      // issues the MMAs of one K-block (nm of 4 K=16 steps)
+      // one K step (32 bytes of each operand row): one MMA, three for bf16x3
+      auto kstep = [&](uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+        if (F == kFormFP8) {
+          ptx::mma_f8(d_tmem, ad, bd, idesc, acc);
+        } else {
+          ptx::mma_bf16(d_tmem, ad, bd, idesc, acc);
+          if (F == kFormBF16x3) {
+            ptx::mma_bf16(d_tmem, ad, bd + b_lo, idesc, 1u);
+            ptx::mma_bf16(d_tmem, ad + a_lo, bd, idesc, 1u);
+          }
+        }
+      };
+      // issues the MMAs of one K-block (nm of 4 K steps)
       auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int nm) {
         const uint64_t ad = adesc0 + st * a_step;
         const uint64_t bd = bdesc0 + (uint32_t)kb * b_step;
         if (nm == 4) {
-          ptx::mma_bf16(d_tmem, ad, bd, idesc, kb != 0);
-          ptx::mma_bf16(d_tmem, ad + 2u, bd + 2u, idesc, 1u);
-          ptx::mma_bf16(d_tmem, ad + 4u, bd + 4u, idesc, 1u);
-          ptx::mma_bf16(d_tmem, ad + 6u, bd + 6u, idesc, 1u);
+          kstep(d_tmem, ad, bd, kb != 0);
+          kstep(d_tmem, ad + 2u, bd + 2u, 1u);
+          kstep(d_tmem, ad + 4u, bd + 4u, 1u);
+          kstep(d_tmem, ad + 6u, bd + 6u, 1u);
         } else {
           for (int kk = 0; kk < nm; ++kk)
-            ptx::mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
+            kstep(d_tmem, ad + 2u * kk, bd + 2u * kk, (kb | kk) != 0);
         }
       };
       for (int it = 0; it < my_tiles && ok; ++it) {
@@ -347,6 +402,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         const int chrom = c * 128 + row;
         const float bias = a.a0[chrom];
         const uint64_t bias2 = ptx::f2_pack(bias, bias);
+        const float negu = F == kFormFP8 ? -a.uscale[chrom] : -1.f;
+        const uint64_t negu2 = ptx::f2_pack(negu, negu);
         uint64_t s2 = 0;   // two FP32 partial sums (even / odd columns)
         float s_tail = 0.f;
         const uint32_t tbase = tmem + lane_addr + buf * (uint32_t)BN + (uint32_t)col_lo;
@@ -360,12 +417,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int k = 0; k < nfull; k += 2) {
             const bool has_b = k + 1 < nfull;
             if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
-            epi_chunk(va, yt + k * 32, bias2, s2);
+            epi_chunk(va, yt + k * 32, bias2, negu2, s2);
             if (has_b) {
               ptx::tmem_ld32_wait(vb);
               const bool has_a = k + 2 < nfull;
               if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
-              epi_chunk(vb, yt + (k + 1) * 32, bias2, s2);
+              epi_chunk(vb, yt + (k + 1) * 32, bias2, negu2, s2);
               if (has_a) ptx::tmem_ld32_wait(va);
             }
           }
@@ -377,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
             if (e < lim) {
-              const float r = (yt[nfull * 32 + e] - bias) - __uint_as_float(v[e]);
+              const float r = fmaf(negu, __uint_as_float(v[e]), yt[nfull * 32 + e] - bias);
               s_tail = fmaf(r, r, s_tail);
             }
           }
@@ -393,76 +450,107 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   } else if (warp >= kBasisWarp0) {
     // ---------------- expansion (basis) ----------------
     const int bt = threadIdx.x - kBasisWarp0 * 32;
-    for (int cid = bt; cid < KB * 8; cid += kBasisThreads)
+    for (int cid = bt; cid < KB * CPK; cid += kBasisThreads)
       tab[cid] = chunk_desc(cid, a.basis, a.d, a.Kp);
+    if (F == kFormFP8)
+      for (int k = bt; k < KB * 128; k += kBasisThreads) cs[k] = a.colinv[k];
     ptx::named_bar(1, kBasisThreads);
-    // thread -> rows r0 + 128 * rr (rr < R) and chunks q0, q0 + QS, ...
+    // thread -> rows r0 + 128 * rr (rr < R) and 16-byte units q0, q0 + QS, ...
     const int RW = BN < 128 ? BN : 128;
     const int R = BN / RW;          // rows per thread (2 when BN = 256)
-    const int QS = 128 / RW;        // chunk stride (1 when BN >= 128)
+    const int QS = 128 / RW;        // unit stride (1 when BN >= 128)
     const int r0 = bt % RW, q0 = bt / RW;
+    const int r1 = r0 + 128;
     const float* xrow0 = xs + (r0 >> 7) * N * XW + (r0 % XW);
-    const float* xrow1 = xs + ((r0 + 128) >> 7) * N * XW + ((r0 + 128) % XW);
-    // one chunk of one row: expansion, BF16 rounding, swizzled 16-byte store
-    auto emit = [&](uint8_t* phik, uint32_t desc, int qd, int r, const float* xr) {
-      float v[8];
-      gen_chunk(desc, a.basis, a.d, N, xr, XW, v);
-      uint32_t w[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
-        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-      *reinterpret_cast<uint4*>(phik + r * 128 + ((qd ^ (r & 7)) << 4)) =
-          make_uint4(w[0], w[1], w[2], w[3]);
-    };
-    // both rows of a Chebyshev chunk that stays in one feature's run of
-    // degrees (the common case: degree 8): two interleaved recurrences, one
-    // descriptor decode, no per-value branches
-    auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
-      const int i = (int)(desc & 0xFFFFu);
-      const int j0 = (int)((desc >> 16) & 31u);
-      const float xa = xrow0[i * XW];
-      const float xb = R == 2 ? xrow1[i * XW] : 0.f;
-      const float a2 = xa + xa, b2 = xb + xb;
-      float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
-      for (int st = 1; st < j0; ++st) {
-        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
-        tam = ta;
-        ta = na;
-        tbm = tb;
-        tb = nb;
-      }
-      float va[8], vb[8];
-      va[0] = ta;
-      vb[0] = tb;
-#pragma unroll
-      for (int e = 1; e < 8; ++e) {
-        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
-        tam = ta;
-        ta = na;
-        tbm = tb;
-        tb = nb;
-        va[e] = ta;
-        vb[e] = tb;
-      }
-      uint32_t wa[4], wb[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const __nv_bfloat162 pa = __floats2bfloat162_rn(va[2 * h], va[2 * h + 1]);
-        const __nv_bfloat162 pb = __floats2bfloat162_rn(vb[2 * h], vb[2 * h + 1]);
-        wa[h] = *reinterpret_cast<const uint32_t*>(&pa);
-        wb[h] = *reinterpret_cast<const uint32_t*>(&pb);
-      }
-      *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
-          make_uint4(wa[0], wa[1], wa[2], wa[3]);
-      if (R == 2) {
-        const int r1 = r0 + 128;
-        *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
-            make_uint4(wb[0], wb[1], wb[2], wb[3]);
-      }
-    };
+    const float* xrow1 = xs + (r1 >> 7) * N * XW + (r1 % XW);
     const bool cheb = a.basis == GAME_BASIS_CHEB;
+    // the 8 values of one chunk for row r0 (va) and, when R == 2, row r1
+    // (vb). A Chebyshev chunk inside one feature's run of degrees (the common
+    // case: degree 8) takes two interleaved recurrences and one descriptor
+    // decode, with no per-value branches.
+    auto gen_rows = [&](uint32_t desc, float (&va)[8], float (&vb)[8]) {
+      if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
+        const int i = (int)(desc & 0xFFFFu);
+        const int j0 = (int)((desc >> 16) & 31u);
+        const float xa = xrow0[i * XW];
+        const float xb = R == 2 ? xrow1[i * XW] : 0.f;
+        const float a2 = xa + xa, b2 = xb + xb;
+        float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
+        for (int st = 1; st < j0; ++st) {
+          const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+          tam = ta;
+          ta = na;
+          tbm = tb;
+          tb = nb;
+        }
+        va[0] = ta;
+        vb[0] = tb;
+#pragma unroll
+        for (int e = 1; e < 8; ++e) {
+          const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+          tam = ta;
+          ta = na;
+          tbm = tb;
+          tb = nb;
+          va[e] = ta;
+          vb[e] = tb;
+        }
+      } else {
+        gen_chunk(desc, a.basis, a.d, N, xrow0, XW, va);
+        if (R == 2) gen_chunk(desc, a.basis, a.d, N, xrow1, XW, vb);
+      }
+    };
+    auto store16 = [&](uint8_t* img, int r, int qd, uint32_t w0, uint32_t w1, uint32_t w2,
+                       uint32_t w3) {
+      *reinterpret_cast<uint4*>(img + r * 128 + ((qd ^ (r & 7)) << 4)) =
+          make_uint4(w0, w1, w2, w3);
+    };
+    // one 16-byte unit qd of K-block kb for the thread's rows
+    auto emit_unit = [&](uint8_t* phik, int kb, int qd) {
+      float va[8], vb[8];
+      if (F == kFormFP8) {
+        // 16 columns: chunks 2 qd and 2 qd + 1, scaled into E4M3's range
+        float vc[8], vd[8];
+        gen_rows(tab[kb * CPK + 2 * qd], va, vb);
+        gen_rows(tab[kb * CPK + 2 * qd + 1], vc, vd);
+        const float* sc = cs + kb * 128 + qd * 16;
+        float s16[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) s16[e] = sc[e];
+        store16(phik, r0, qd, e4m3x4_bits(va[0] * s16[0], va[1] * s16[1], va[2] * s16[2], va[3] * s16[3]),
+                e4m3x4_bits(va[4] * s16[4], va[5] * s16[5], va[6] * s16[6], va[7] * s16[7]),
+                e4m3x4_bits(vc[0] * s16[8], vc[1] * s16[9], vc[2] * s16[10], vc[3] * s16[11]),
+                e4m3x4_bits(vc[4] * s16[12], vc[5] * s16[13], vc[6] * s16[14], vc[7] * s16[15]));
+        if (R == 2)
+          store16(phik, r1, qd,
+                  e4m3x4_bits(vb[0] * s16[0], vb[1] * s16[1], vb[2] * s16[2], vb[3] * s16[3]),
+                  e4m3x4_bits(vb[4] * s16[4], vb[5] * s16[5], vb[6] * s16[6], vb[7] * s16[7]),
+                  e4m3x4_bits(vd[0] * s16[8], vd[1] * s16[9], vd[2] * s16[10], vd[3] * s16[11]),
+                  e4m3x4_bits(vd[4] * s16[12], vd[5] * s16[13], vd[6] * s16[14], vd[7] * s16[15]));
+      } else {
+        gen_rows(tab[kb * CPK + qd], va, vb);
+        if (F == kFormBF16) {
+          store16(phik, r0, qd, bf16x2_bits(va[0], va[1]), bf16x2_bits(va[2], va[3]),
+                  bf16x2_bits(va[4], va[5]), bf16x2_bits(va[6], va[7]));
+          if (R == 2)
+            store16(phik, r1, qd, bf16x2_bits(vb[0], vb[1]), bf16x2_bits(vb[2], vb[3]),
+                    bf16x2_bits(vb[4], vb[5]), bf16x2_bits(vb[6], vb[7]));
+        } else {
+          uint8_t* phik_lo = phik + BN * 128;
+          uint32_t h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split_bf16x2(va[2 * e], va[2 * e + 1], h[e], l[e]);
+          store16(phik, r0, qd, h[0], h[1], h[2], h[3]);
+          store16(phik_lo, r0, qd, l[0], l[1], l[2], l[3]);
+          if (R == 2) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) split_bf16x2(vb[2 * e], vb[2 * e + 1], h[e], l[e]);
+            store16(phik, r1, qd, h[0], h[1], h[2], h[3]);
+            store16(phik_lo, r1, qd, l[0], l[1], l[2], l[3]);
+          }
+        }
+      }
+    };
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
       ok = wait_bar(ptx::smem_addr(x_full), it & 1, abort_flag, a.status);
@@ -472,16 +560,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           ok = wait_bar(ptx::smem_addr(&phi_free[kb]), (it - 1) & 1, abort_flag, a.status);
           if (!ok) break;
         }
-        uint8_t* phik = phi + (size_t)kb * BN * 128;
-        for (int qd = q0; qd < 8; qd += QS) {
-          const uint32_t desc = tab[kb * 8 + qd];
-          if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
-            emit_cheb_run2(phik, desc, qd);
-          } else {
-            emit(phik, desc, qd, r0, xrow0);
-            if (R == 2) emit(phik, desc, qd, r0 + 128, xrow1);
-          }
-        }
+        uint8_t* phik = phi + (size_t)kb * NPHI * BN * 128;
+        for (int qd = q0; qd < 8; qd += QS) emit_unit(phik, kb, qd);
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));
       }
@@ -500,15 +580,18 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 
 }  // namespace
 
-TcPlan plan_tc(const Shape& s, int P, int num_sms) {
+TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
   TcPlan pl{};
-  pl.KB = ceil_div(s.Kp, 64);
+  pl.form = form;
+  pl.KB = ceil_div(s.Kp, form_cols(form));
   pl.C = ceil_div(P, 128);
   pl.ok = false;
   const int cands[4] = {256, 128, 64, 32};
+  // bf16x3 doubles both operands, so it may fall back to two gene stages
+  const int min_stages = form == kFormBF16x3 ? 2 : 3;
   for (int i = 0; i < 4 && !pl.ok; ++i) {
-    for (int stages = 4; stages >= 3; --stages) {
-      const int sm = smem_plan(pl.KB, cands[i], s.N, stages).total;
+    for (int stages = 4; stages >= min_stages; --stages) {
+      const int sm = smem_plan(pl.KB, cands[i], s.N, stages, form).total;
       if (sm <= kMaxSmem) {
         pl.BN = cands[i];
         pl.stages = stages;
@@ -531,8 +614,9 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms) {
 }
 
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
-                              const float* y, const uint8_t* popA, const float* a0, int P,
-                              int Ppad, double* part, int* status, cudaStream_t st) {
+                              const float* y, const uint8_t* popA, const float* a0,
+                              const float* uscale, const float* colinv, int P, int Ppad,
+                              double* part, int* status, cudaStream_t st) {
   (void)P;
   if (!pl.ok) return cudaErrorInvalidValue;
   TcArgs a;
@@ -545,8 +629,9 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.KB = pl.KB;
   a.C = pl.C;
   a.stages = pl.stages;
-  const int last_cols = s.Kp - 64 * (pl.KB - 1);
-  a.nmma_last = (last_cols + 15) / 16;
+  const int cols = form_cols(pl.form);
+  const int last_cols = s.Kp - cols * (pl.KB - 1);
+  a.nmma_last = (last_cols + cols / 4 - 1) / (cols / 4);
   a.ntiles = (int)(s.Mpad / pl.BN);
   a.Ppad = Ppad;
   a.tmem_cols = pl.tmem_cols;
@@ -554,13 +639,18 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.y = y;
   a.popA = popA;
   a.a0 = a0;
+  a.uscale = uscale;
+  a.colinv = colinv;
   a.part = part;
   a.status = status;
-  cudaError_t e = cudaFuncSetAttribute(fitness_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (pl.form == kFormFP8 && (!uscale || !colinv)) return cudaErrorInvalidValue;
+  void (*kern)(const TcArgs) = pl.form == kFormBF16x3 ? fitness_tc_kernel<kFormBF16x3>
+                               : pl.form == kFormFP8  ? fitness_tc_kernel<kFormFP8>
+                                                      : fitness_tc_kernel<kFormBF16>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        pl.smem_bytes);
   if (e != cudaSuccess) return e;
-  fitness_tc_kernel<<<pl.grid, kThreads, pl.smem_bytes, st>>>(a);
+  kern<<<pl.grid, kThreads, pl.smem_bytes, st>>>(a);
   return cudaGetLastError();
 }
 

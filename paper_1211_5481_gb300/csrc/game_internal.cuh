@@ -11,10 +11,15 @@
 //   fit  [P] FP64                 fitness of the current population.
 // Evaluation scratch (grown on demand):
 //   popT [Kc][Ppad] FP32          genes 1..K-1 transposed (CUDA-core form).
-//   popA [C][KB][128][64] BF16    genes 1..K-1 in the tcgen05 K-major SWIZZLE_128B
-//                                 operand image: one 16 KB block per (chromosome
+//   popA [C][KB][na][128][128 B]  genes 1..K-1 in the tcgen05 K-major SWIZZLE_128B
+//                                 operand image: na 16 KB blocks per (chromosome
 //                                 tile c, K-block kb), bulk-copied unchanged into
-//                                 shared memory.
+//                                 shared memory. BF16: 64 columns per row; bf16x3:
+//                                 the hi block then the lo block; FP8 E4M3: 128
+//                                 columns per row, genes scaled by colscale[k]
+//                                 and 1 / uscale[p].
+//   uscale [Ppad] FP32            FP8: per-chromosome scale restored in the epilogue.
+//   colscale, colinv [KB*128]     FP8: per-column scales of the expansion (handle-lifetime).
 //   a0   [Ppad] FP32              bias genes.
 //   part [rows][Ppad] FP64        per-CTA partial sums of squared residuals.
 // Elite re-scoring (fixed size, allocated with the handle):
@@ -53,20 +58,36 @@ cudaError_t launch_relayout_X(const float* X, const float* y, const Shape& s, fl
                               float* yp, int* bad_counts, cudaStream_t st);
 cudaError_t launch_pack_fp32(const float* pop, int P, int Ppad, const Shape& s, int Kc,
                              float* popT, float* a0, cudaStream_t st);
-cudaError_t launch_pack_bf16(const float* pop, int P, int C, const Shape& s, int KB,
-                             uint8_t* popA, float* a0, cudaStream_t st);
 // fitness_fp32.cu
 struct Fp32Plan { int BP, BM, Kc, grid_x, grid_y; };
 Fp32Plan plan_fp32(const Shape& s, int P, int num_sms);
 cudaError_t launch_fitness_fp32(const Fp32Plan& pl, const Shape& s, const float* Xt,
                                 const float* y, const float* popT, const float* a0, int P,
                                 int Ppad, double* part, cudaStream_t st);
-// fitness_tc.cu
-struct TcPlan { int BN, KB, NS, C, stages, grid, smem_bytes, tmem_cols, rows; bool ok; };
-TcPlan plan_tc(const Shape& s, int P, int num_sms);
+// fitness_tc.cu -- operand forms of the tensor-core contraction
+enum TcForm : int { kFormBF16 = 0, kFormBF16x3 = 1, kFormFP8 = 2 };
+// 16 KB gene blocks per (chromosome tile, K-block): hi and lo for bf16x3
+__host__ __device__ constexpr int form_na(int f) { return f == kFormBF16x3 ? 2 : 1; }
+// expansion images per K-block: hi and lo for bf16x3
+__host__ __device__ constexpr int form_nphi(int f) { return f == kFormBF16x3 ? 2 : 1; }
+// contraction columns per K-block (one 128-byte swizzled row)
+__host__ __device__ constexpr int form_cols(int f) { return f == kFormFP8 ? 128 : 64; }
+struct TcPlan { int form, BN, KB, NS, C, stages, grid, smem_bytes, tmem_cols, rows; bool ok; };
+TcPlan plan_tc(const Shape& s, int P, int num_sms, int form);
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
-                              const float* y, const uint8_t* popA, const float* a0, int P,
-                              int Ppad, double* part, int* status, cudaStream_t st);
+                              const float* y, const uint8_t* popA, const float* a0,
+                              const float* uscale, const float* colinv, int P, int Ppad,
+                              double* part, int* status, cudaStream_t st);
+// layout.cu: FP8 column scales. colmax [KB*128] receives max_m |phi_k(x_m)|
+// as FP32 bit patterns (zero-initialised by the caller); scales turns it into
+// colscale = colmax / 448 and colinv = 448 / colmax (0 where colmax is 0).
+cudaError_t launch_colmax(const Shape& s, const float* Xt, unsigned int* colmax, int ncols,
+                          cudaStream_t st);
+cudaError_t launch_colscales(const unsigned int* colmax, int ncols, float* colscale,
+                             float* colinv, cudaStream_t st);
+cudaError_t launch_pack_tc(int form, const float* pop, int P, int C, const Shape& s, int KB,
+                           const float* colscale, uint8_t* popA, float* a0, float* uscale,
+                           cudaStream_t st);
 // rescore.cu
 struct RescorePlan { int pt, grid; };   // patterns per thread, CTAs per candidate group
 RescorePlan plan_rescore(const Shape& s, int num_sms);

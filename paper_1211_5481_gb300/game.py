@@ -26,6 +26,8 @@ GAME_BASIS_CHEB = 0
 GAME_BASIS_TRIG = 1
 GAME_PREC_FP32 = 0
 GAME_PREC_BF16 = 1
+GAME_PREC_BF16X3 = 2
+GAME_PREC_FP8 = 3
 
 _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
               GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}

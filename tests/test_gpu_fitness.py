@@ -7,7 +7,7 @@ FP32 contraction (helpers.bf16_bound), and its relative error is reported.
 import numpy as np
 import pytest
 
-from helpers import CHEB, TRIG, bf16_bound, fp32_tol
+from helpers import CHEB, TRIG, bf16_bound, bf16x3_bound, fp32_tol, fp8_bound
 from paper_1211_5481_gb300 import datagen as dg
 from paper_1211_5481_gb300 import game
 
@@ -15,6 +15,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 FP32, BF16 = game.GAME_PREC_FP32, game.GAME_PREC_BF16
+BF16X3, FP8 = game.GAME_PREC_BF16X3, game.GAME_PREC_FP8
+BOUNDS = {BF16: bf16_bound, BF16X3: bf16x3_bound, FP8: fp8_bound}
 
 # (M, N, d, basis, P): tile multiples, ragged tails, K not a multiple of 16,
 # P below / above / not a multiple of 128, tiny and long contractions
@@ -44,18 +46,24 @@ def dev():
 
 
 @pytest.mark.parametrize("case", CASES, ids=[str(c) for c in CASES])
-@pytest.mark.parametrize("prec", [FP32, BF16], ids=["fp32", "bf16"])
+@pytest.mark.parametrize("prec", [FP32, BF16, BF16X3, FP8], ids=["fp32", "bf16", "bf16x3", "fp8"])
 def test_fitness_matches_oracle(orc, dev, case, prec):
     M, N, d, basis, P = case
     pr = make_problem(M, N, d, basis, seed=M + N + d)
     pop = dg.random_population(7 + P, P, pr.K)
     ref = orc.fitness(pr.X, pr.y, pop, d, basis)
+    if prec == BF16X3 and pr.K - 1 > 1216:
+        # both split operands no longer fit in shared memory: rejected
+        with pytest.raises(game.GameError) as ei:
+            game.Game(pr.X, pr.y, d, basis, P=max(P, 4), precision=prec)
+        assert ei.value.code == game.GAME_EINVAL
+        return
     with game.Game(pr.X, pr.y, d, basis, P=max(P, 4), precision=prec) as g:
         got = g.eval_fitness(pop)
     if prec == FP32:
         tol = fp32_tol(ref, pr.y)
     else:
-        tol = bf16_bound(ref, pr.X, pop, d, basis)
+        tol = BOUNDS[prec](ref, pr.X, pop, d, basis)
     err = np.abs(got - ref)
     assert np.all(err <= tol), (f"max err {err.max():.3e}, worst ratio "
                                 f"{(err / tol).max():.3f}, rel {np.max(err / np.abs(ref)):.3e}")
@@ -92,7 +100,7 @@ def test_converged_population(orc, dev):
 def test_deterministic(dev):
     pr = dg.regression(5, 3000, 12, 4, 0.05, degree=5)
     pop = dg.random_population(4, 200, pr.K)
-    for prec in (FP32, BF16):
+    for prec in (FP32, BF16, BF16X3, FP8):
         with game.Game(pr.X, pr.y, 5, CHEB, P=200, precision=prec) as g:
             a = g.eval_fitness(pop)
             b = g.eval_fitness(pop)
@@ -113,10 +121,13 @@ def test_full_size_sampled(orc, dev):
     with game.Game(Xd, yd, pr.degree, CHEB, P=P) as g:
         f32 = g.eval_fitness(pop)
         fbf = g.eval_fitness(pop, precision=BF16)
+        fx3 = g.eval_fitness(pop, precision=BF16X3)
+        ff8 = g.eval_fitness(pop, precision=FP8)
     assert np.all(np.abs(f32[sample] - ref) <= fp32_tol(ref, pr.y))
-    bound = bf16_bound(ref, pr.X[::50], pop[sample], pr.degree, CHEB)
-    # the bound uses every 50th pattern for its mean of S^2: allow 10% for that
-    assert np.all(np.abs(fbf[sample] - ref) <= 1.1 * bound)
+    # the bounds use every 50th pattern for their means of S: allow 10% for that
+    for got, bound in ((fbf, bf16_bound), (fx3, bf16x3_bound), (ff8, fp8_bound)):
+        b = bound(ref, pr.X[::50], pop[sample], pr.degree, CHEB)
+        assert np.all(np.abs(got[sample] - ref) <= 1.1 * b)
     # all chromosomes: the two GPU forms agree within the BF16 bound scale
     rel = np.abs(fbf - f32) / f32
     assert np.median(rel) < 1e-2

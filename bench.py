@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-fp32-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--precision-report", type=int, default=4, metavar="G",
+                    help="generations of the per-form accuracy report (0 = off)")
     return ap.parse_args()
 
 
@@ -133,6 +135,39 @@ def oracle_sample_rate(pr, P_s, target_s=8.0, max_s=25.0):
     return {"value": M_s * P_s / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {M_s} patterns x {P_s} chromosomes of the workload, "
                       f"direct-form FP64 fitness, {dt:.2f} s"}, M_s
+
+
+def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
+    """Accuracy of every contraction form against the FP64 oracle, per
+    generation of the GA run held by handle g: the current population is
+    evaluated on the first M_sub patterns by each form (a handle on that
+    subset) and by the oracle; reported per form and generation: the max and
+    median relative fitness error and the overlap of the form's 10 best with
+    the oracle's 10 best."""
+    import oracle
+    oracle.build()
+    forms = {"fp32": game.GAME_PREC_FP32, "bf16": game.GAME_PREC_BF16,
+             "bf16x3": game.GAME_PREC_BF16X3, "fp8": game.GAME_PREC_FP8}
+    Xs, ys = pr.X[:M_sub], pr.y[:M_sub]
+    sub = game.Game(Xs, ys, pr.degree, pr.basis, P=g.P, precision=game.GAME_PREC_FP32)
+    rows = {f: [] for f in forms}
+    gens = []
+    for step in range(G):
+        pop, _, gen = g.population()
+        ref = oracle.fitness(Xs, ys, pop, pr.degree, pr.basis)
+        best = set(np.argsort(ref, kind="stable")[:10])
+        for name, prec in forms.items():
+            f = sub.eval_fitness(pop, precision=prec)
+            rel = np.abs(f - ref) / np.abs(ref)
+            rows[name].append({"max_rel_err": float(rel.max()),
+                               "median_rel_err": float(np.median(rel)),
+                               "top10_agreement": len(best & set(np.argsort(f, kind="stable")[:10]))
+                               / 10})
+        gens.append(int(gen))
+        if step + 1 < G:
+            game.game_generation(g.h, seed)
+    sub.close()
+    return {"subset_patterns": M_sub, "generations": gens, "forms": rows}
 
 
 def workload(M):
@@ -319,6 +354,8 @@ def main():
                "top10_agreement_form_vs_fp32": len(set(np.argsort(f_bf)[:10]) &
                                                     set(np.argsort(f_32)[:10])) / 10}
         cpu, _ = oracle_sample_rate(pr, 16)
+        if args.precision_report > 0:
+            acc["precision_forms"] = precision_report(game, g, pr, args.precision_report)
 
     n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
         2 * tm["operators_launches"] + 2 * tm["rescore_launches"]

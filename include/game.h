@@ -210,6 +210,55 @@ int game_eval_fitness_static(const float* X, const float* y, int64_t M,
                              const float* pop, int32_t P, double* fit_out,
                              void* cuda_stream);
 
+/* ---- Batched runs ----
+ * Many independent GA runs, each the method above on its own training set,
+ * degree, basis, population size and seed, advanced together: one launch
+ * per stage for all runs (operators, operand pack, fused fitness, FP64
+ * reduce), the stages of a generation replayed from a CUDA graph. The
+ * contraction is BF16 on the tensor cores (GAME_PREC_BF16), the GA state
+ * FP32. Run r with seed s follows the operators of a single handle keyed by
+ * s given the same fitness values. */
+typedef struct game_batch* game_batch_t;
+
+typedef struct {
+  const float* X;   /* [M][N] FP32 features (host or device; copied) */
+  const float* y;   /* [M] FP32 targets */
+  int64_t M;
+  int32_t N, degree, basis;
+  int32_t P;        /* chromosomes, elitism + immigrants + 2 .. 2^20 */
+  uint64_t seed;    /* the run's Philox key */
+} game_run_desc;
+
+/* Creates a batch of R runs. prm gives the GA settings shared by all runs
+ * (elitism, tournament, pc, pm, sigma, immigrants; its P, precision, seed,
+ * rescore_top and stop threshold are ignored). tiles: the pattern-tile width
+ * of each run's fitness items (32, 64, 128 or 256; NULL = choose): with
+ * autotune != 0 the widths are timed per group of runs with the same
+ * K-block count class and chromosome-tile count and the fastest kept, else
+ * the widest that fits. Fitness values depend on the tile width in their
+ * last bits (FP32 sums inside a tile): pass the widths game_batch_get_tiles
+ * returns to reproduce a run exactly. Validation as game_create per run
+ * (GAME_EINVAL naming the run), plus K - 1 <= 2048 and N <= 256. The initial
+ * populations are generated and evaluated. Synchronous. */
+int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* prm,
+                      const int32_t* tiles, int32_t autotune, void* cuda_stream,
+                      game_batch_t* out);
+/* One generation of every run (one graph launch). Enqueues only. */
+int game_batch_generation(game_batch_t b);
+/* Population [P_r][K_r], fitness [P_r] and generation of run r (host or
+ * device outputs; any may be NULL). Synchronises. */
+int game_batch_get_run(game_batch_t b, int32_t r, float* pop_out, double* fit_out,
+                       int64_t* generation);
+/* The tile width of every run, tiles_out[R]. */
+int game_batch_get_tiles(game_batch_t b, int32_t* tiles_out);
+/* Mean device time of the batched fitness launch over reps launches on the
+ * current populations (CUDA events on the batch's stream). Synchronises. */
+int game_batch_fitness_ms(game_batch_t b, int32_t reps, double* ms_out);
+/* Waits for the batch's stream and reports a kernel timeout, if any. */
+int game_batch_sync(game_batch_t b);
+/* Releases the batch (NULL is accepted). */
+int game_batch_destroy(game_batch_t b);
+
 /* Waits for the handle's stream and reports a kernel timeout, if any. */
 int game_sync(game_t h);
 

@@ -88,6 +88,31 @@ cudaError_t launch_colscales(const unsigned int* colmax, int ncols, float* colsc
 cudaError_t launch_pack_tc(int form, const float* pop, int P, int C, const Shape& s, int KB,
                            const float* colscale, uint8_t* popA, float* a0, float* uscale,
                            cudaStream_t st);
+// batch_tc.cu -- many problems in one persistent tensor-core launch (BF16)
+struct BatchRun {           // one problem, as the batched kernels see it
+  const float* Xt;          // [Mpad/128][N][128]
+  const float* y;           // [Mpad]
+  const uint8_t* popA;      // [C][KB][128][128 B] BF16 operand image
+  const float* a0;          // [Ppad]
+  int64_t M;
+  int64_t part_base;        // first partial row of this problem (doubles)
+  int N, d, basis, Kp, K, P, Ppad, C, KB, BN, nmma_last, ntiles;
+};
+struct BatchArgs {
+  const BatchRun* runs;
+  const int2* items;        // (problem, pattern tile), problem-major
+  const int* sched;         // item indices, grouped by CTA
+  const int* cta_begin;     // [grid + 1] ranges of sched per CTA
+  double* part;             // partial rows: part_base_r + (2 t + half) Ppad_r
+  int* status;
+  int KBmax, bn_max, phi_bytes, x_bytes, tmem_cols;
+};
+int batch_smem_bytes(int phi_bytes, int x_bytes, int KBmax);
+// sets the kernel's dynamic shared-memory limit (call outside stream capture)
+cudaError_t prepare_fitness_batch(int smem_bytes);
+// launch only (capturable)
+cudaError_t launch_fitness_batch(const BatchArgs& a, int grid, int smem_bytes, cudaStream_t st);
+
 // rescore.cu
 struct RescorePlan { int pt, grid; };   // patterns per thread, CTAs per candidate group
 RescorePlan plan_rescore(const Shape& s, int num_sms);

@@ -36,7 +36,10 @@ _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA
 EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_fitness",
             "game_eval_fitness_prec", "game_generation", "game_train", "game_get_population",
             "game_set_state", "game_set_timing", "game_get_timing", "game_sync",
-            "game_destroy", "game_last_error", "game_eval_fitness_static", "game_rescore_top")
+            "game_destroy", "game_last_error", "game_eval_fitness_static", "game_rescore_top",
+            "game_batch_create", "game_batch_generation", "game_batch_get_run",
+            "game_batch_get_tiles", "game_batch_fitness_ms", "game_batch_sync",
+            "game_batch_destroy")
 
 
 class GameError(RuntimeError):
@@ -79,6 +82,19 @@ class game_timing(ctypes.Structure):
     ]
 
 
+class game_run_desc(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("M", ctypes.c_int64),
+        ("N", ctypes.c_int32),
+        ("degree", ctypes.c_int32),
+        ("basis", ctypes.c_int32),
+        ("P", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 _lib = None
 
 
@@ -116,6 +132,14 @@ def load(build_if_missing: bool = True):
         "game_destroy": [vp],
         "game_eval_fitness_static": [vp, vp, i64, i32, i32, i32, vp, i32, dp, vp],
         "game_rescore_top": [vp, vp, i32, dp, i32, vp],
+        "game_batch_create": [ctypes.POINTER(game_run_desc), i32, ctypes.POINTER(game_params),
+                              vp, i32, vp, ctypes.POINTER(vp)],
+        "game_batch_generation": [vp],
+        "game_batch_get_run": [vp, i32, vp, dp, ctypes.POINTER(i64)],
+        "game_batch_get_tiles": [vp, vp],
+        "game_batch_fitness_ms": [vp, i32, ctypes.POINTER(ctypes.c_double)],
+        "game_batch_sync": [vp],
+        "game_batch_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -301,6 +325,81 @@ class Game:
     def close(self):
         if self.h:
             game_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Owning wrapper of a batch of independent runs (game_batch_*).
+
+    runs: sequence of (X, y, degree, basis, P, seed) with X [M][N] float32 and
+    y [M] float32 numpy arrays or CUDA tensors."""
+
+    def __init__(self, runs, tiles=None, autotune=True, stream=None, **params):
+        prm = game_params_default()
+        for k, v in params.items():
+            setattr(prm, k, v)
+        descs = (game_run_desc * len(runs))()
+        self._keep = []
+        self.shapes = []
+        for r, (X, y, degree, basis, P, seed) in enumerate(runs):
+            if isinstance(X, np.ndarray):
+                X = np.ascontiguousarray(X, dtype=np.float32)
+                y = np.ascontiguousarray(y, dtype=np.float32)
+            self._keep.append((X, y))
+            M, N = X.shape
+            descs[r] = game_run_desc(_ptr(X), _ptr(y), M, N, degree, basis, P, seed)
+            B = 2 if basis == GAME_BASIS_TRIG else 1
+            self.shapes.append((M, N, B * N * degree + 1, P))
+        t = None
+        if tiles is not None:
+            t = np.ascontiguousarray(tiles, dtype=np.int32)
+            self._keep.append(t)
+        h = ctypes.c_void_p()
+        _check(load().game_batch_create(descs, len(runs), ctypes.byref(prm),
+                                        _ptr(t) if t is not None else None, int(bool(autotune)),
+                                        _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.R = len(runs)
+
+    def generation(self):
+        _check(load().game_batch_generation(self.h))
+
+    def run(self, r):
+        M, N, K, P = self.shapes[r]
+        pop = np.zeros((P, K), dtype=np.float32)
+        fit = np.zeros(P, dtype=np.float64)
+        g = ctypes.c_int64()
+        _check(load().game_batch_get_run(self.h, r, _ptr(pop), _ptr(fit), ctypes.byref(g)))
+        return pop, fit, g.value
+
+    def tiles(self):
+        t = np.zeros(self.R, dtype=np.int32)
+        _check(load().game_batch_get_tiles(self.h, _ptr(t)))
+        return t
+
+    def fitness_ms(self, reps=10):
+        ms = ctypes.c_double()
+        _check(load().game_batch_fitness_ms(self.h, reps, ctypes.byref(ms)))
+        return ms.value
+
+    def sync(self):
+        _check(load().game_batch_sync(self.h))
+
+    def close(self):
+        if self.h:
+            _check(load().game_batch_destroy(self.h))
             self.h = None
 
     def __del__(self):

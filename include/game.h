@@ -88,7 +88,11 @@ typedef struct {
                            the rescore_top best chromosomes are re-scored as
                            game_rescore_top does, before the operators rank
                            them; 0 = off */
-  int32_t reserved[7];  /* must be zero */
+  int32_t surrogate;    /* 1: screen oversampled offspring with the fitness
+                           surrogate (game_surrogate_*), 0: off */
+  int32_t oversample;   /* offspring per kept child when screening (>= 1,
+                           oversample * (P - elitism) <= 16384) */
+  int32_t reserved[5];  /* must be zero */
 } game_params;
 
 /* Fills *out with the defaults listed above (and rescore_top = 8). */
@@ -179,6 +183,8 @@ typedef struct {
   int64_t operators_launches; /* calls; two kernels each */
   double rescore_ms;        /* elite candidate selection and re-scoring */
   int64_t rescore_launches; /* calls; two kernels each */
+  double surrogate_ms;      /* surrogate screening and training */
+  int64_t surrogate_launches; /* generations screened */
 } game_timing;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */
@@ -209,6 +215,40 @@ int game_eval_fitness_static(const float* X, const float* y, int64_t M,
                              int32_t N, int32_t degree, int32_t basis,
                              const float* pop, int32_t P, double* fit_out,
                              void* cuda_stream);
+
+/* ---- Fitness surrogate ----
+ * Not in the paper: a small MLP (genes -> 256 -> 256 -> 1, GELU, BF16
+ * operands with FP32 accumulation in the two hidden layers, FP32 master
+ * weights, Adam lr 1e-3) that predicts log(MSE) of a chromosome. With
+ * prm->surrogate, every generation breeds oversample * (P - E) children with
+ * the operators of game_generation (tournaments from the current
+ * population), keeps the P - E children with the lowest predicted fitness
+ * (ties by slot) in slot order after the E elites, evaluates that population
+ * exactly (the handle's precision and re-scoring), and then trains the
+ * surrogate with one Adam step on each of the last two generations' exact
+ * (chromosome, fitness) pairs. The surrogate of a fresh handle is initialised
+ * from prm->seed and trained with 20 steps on generation 0.
+ * Parameter vector (FP32): W1 [256][K], b1 [256], W2 [256][256], b2 [256],
+ * w3 [256], b3 [1]. Arrays may be host or device memory. */
+/* Predictions for n chromosomes pop [n][K] into pred_out [n] (FP32, the
+ * log-fitness scale). */
+int game_surrogate_predict(game_t h, const float* pop, int32_t n, float* pred_out);
+/* Gradient of the training loss mean((out - log fit)^2) over the pairs
+ * (pop [n][K], fit [n]) at the current parameters, into grad_out [count];
+ * loss_out (may be NULL) receives the loss. Parameters are not changed. */
+int game_surrogate_grad(game_t h, const float* pop, const double* fit, int32_t n,
+                        float* grad_out, float* loss_out);
+/* One Adam step on the pairs (pop [n][K], fit [n]). */
+int game_surrogate_train(game_t h, const float* pop, const double* fit, int32_t n);
+/* The parameter count (count may not be NULL) and, if w_out is not NULL, the
+ * FP32 parameters. */
+int game_surrogate_params(game_t h, float* w_out, int64_t* count);
+/* Replaces the parameters (w [count]) and resets the Adam state. */
+int game_surrogate_set_params(game_t h, const float* w);
+/* The last screening: *n_out children (slot E + i), their predictions
+ * pred_out [n] and kept flags keep_out [n] (any output may be NULL; pass
+ * NULL arrays first to learn n). */
+int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out);
 
 /* ---- Batched runs ----
  * Many independent GA runs, each the method above on its own training set,

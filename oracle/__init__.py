@@ -90,6 +90,8 @@ def _load():
         lib.oracle_train.argtypes = [vp, vp, i64, i32, i32, i32, i32,
                                      ctypes.POINTER(GAParams), u64, i32, i32, vp, vp, vp]
         lib.oracle_select_best.argtypes = [vp, i32, i32, vp]
+        lib.oracle_offspring.argtypes = [vp, vp, i32, i32, ctypes.POINTER(GAParams), u64, u32,
+                                         i32, vp]
         lib.oracle_rescore.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp, i32, vp, vp]
         lib.oracle_set_threads.argtypes = [i32]
         _lib = lib
@@ -230,6 +232,18 @@ def rescore(X, y, pop, d, basis, fit, n):
     _check(_load().oracle_rescore(_ptr(X), _ptr(y), M, N, d, basis, _ptr(pop), P, _ptr(fit),
                                   n, _ptr(out), _ptr(idx)), "rescore")
     return out, idx
+
+
+def offspring(pop, fit, seed, g, n_out, prm=None):
+    """The generation's operators with n_out output slots (oversampling)."""
+    prm = prm or ga_params()
+    pop = np.ascontiguousarray(pop, dtype=np.float32)
+    fit = _f64(fit)
+    P, K = pop.shape
+    nxt = np.zeros((n_out, K), dtype=np.float32)
+    _check(_load().oracle_offspring(_ptr(pop), _ptr(fit), P, K, ctypes.byref(prm), seed, g,
+                                    n_out, _ptr(nxt)), "offspring")
+    return nxt
 
 
 def train(X, y, d, basis, P, G, seed, prm=None, use_gram=False):

@@ -301,9 +301,15 @@ static float irwin_hall_12(uint64_t seed, uint32_t g, uint32_t s, uint32_t k) {
 int oracle_generation(const float* pop, const double* fit, int32_t P,
                       int32_t K, const oracle_ga_params* prm, uint64_t seed,
                       uint32_t g, float* next) {
+  return oracle_offspring(pop, fit, P, K, prm, seed, g, P, next);
+}
+
+int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
+                     const oracle_ga_params* prm, uint64_t seed, uint32_t g,
+                     int32_t n_out, float* next) {
   if (!pop || !fit || !next || !prm || K < 1) return -1;
   const int32_t E = prm->elitism, T = prm->tournament, I = prm->immigrants;
-  if (E < 0 || T < 1 || I < 0 || P < E + I + 2) return -1;
+  if (E < 0 || T < 1 || I < 0 || P < E + I + 2 || n_out < E + I + 2) return -1;
 
   /* 1. Elitism: the E best by (fitness, index) are copied unchanged. */
   int32_t* chosen = (int32_t*)calloc((size_t)P, sizeof(int32_t));
@@ -318,8 +324,9 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
   }
   free(chosen);
 
-  /* 2.-3. Pairs of tournament winners, one-point crossover. */
-  const int32_t npairs = (P - E + 1) / 2;
+  /* 2.-3. Pairs of tournament winners (drawn from the P current
+   * chromosomes), one-point crossover, children in slots E.. n_out-1. */
+  const int32_t npairs = (n_out - E + 1) / 2;
   for (int32_t q = 0; q < npairs; ++q) {
     int32_t parent[2];
     for (int r = 0; r < 2; ++r) {
@@ -343,7 +350,7 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
     const float* p1 = pop + (int64_t)parent[1] * K;
     for (int c = 0; c < 2; ++c) {
       const int32_t slot = E + 2 * q + c;
-      if (slot >= P) continue;
+      if (slot >= n_out) continue;
       const float* head = c == 0 ? p0 : p1;
       const float* tail = c == 0 ? p1 : p0;
       float* child = next + (int64_t)slot * K;
@@ -352,7 +359,7 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
   }
 
   /* 4. Per-gene Gaussian mutation of every non-elite slot, then clamp. */
-  for (int32_t s = E; s < P; ++s)
+  for (int32_t s = E; s < n_out; ++s)
     for (int32_t k = 0; k < K; ++k) {
       uint32_t w[4];
       draw(seed, g, (uint32_t)s, (uint32_t)k, TAG_MUT, w);
@@ -366,7 +373,7 @@ int oracle_generation(const float* pop, const double* fit, int32_t P,
     }
 
   /* 5. Immigrants: the last I slots are replaced by fresh random genes. */
-  for (int32_t s = P - I; s < P; ++s)
+  for (int32_t s = n_out - I; s < n_out; ++s)
     for (int32_t k = 0; k < K; ++k) {
       uint32_t w[4];
       draw(seed, g, (uint32_t)s, (uint32_t)k, TAG_IMM, w);

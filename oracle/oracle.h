@@ -109,6 +109,14 @@ int oracle_rescore(const double* X, const double* y, int64_t M, int32_t N,
                    const double* fit_in, int32_t n, double* fit_out,
                    int32_t* idx);
 
+/* The operators of oracle_generation with n_out output slots instead of P
+ * (oversampled offspring): slots 0..E-1 the elites, E..n_out-1 children of
+ * tournaments drawn from the P current chromosomes, the last I slots
+ * immigrants; next[n_out][K]. n_out = P is oracle_generation. */
+int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
+                     const oracle_ga_params* prm, uint64_t seed, uint32_t g,
+                     int32_t n_out, float* next);
+
 /* Whole GA run: init, then G times (fitness, generation), with the fitness
  * computed by the direct form (use_gram = 0) or the Gram form (1).
  * best[G+1] receives the best fitness after init and after each generation.

@@ -102,6 +102,22 @@ struct game_ctx {
   double* ufit = nullptr;
   int ucap = 0;
   size_t popT_cap = 0, popA_cap = 0;
+  // fitness surrogate
+  SurrogateDev sd{};
+  bool sd_params = false;     // parameters allocated
+  float* off = nullptr;       // offspring [Nout][K]
+  int4* oplan = nullptr;      // their plan [Nout]
+  float* pred = nullptr;      // predictions of the children [kScreenMax]
+  int* flag = nullptr;
+  int* pos = nullptr;
+  int last_n = 0;             // children screened by the last generation
+  float* rX[2] = {nullptr, nullptr};     // replay: the last two populations
+  double* rfit[2] = {nullptr, nullptr};  // and their exact fitness
+  int ring_n = 0, ring_head = 0;
+  float* uX = nullptr;        // device copies of caller arrays
+  double* ufitd = nullptr;
+  float* upred = nullptr;
+  int sur_cap = 0;
   // per-stage timing
   bool timing = false;
   struct Span {
@@ -109,13 +125,20 @@ struct game_ctx {
     int kind;
   };
   std::vector<Span> spans;
-  double tot_ms[5] = {0, 0, 0, 0, 0};
-  int64_t count[5] = {0, 0, 0, 0, 0};
+  double tot_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t count[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
 
-enum StageKind { kFitness = 0, kPack = 1, kReduce = 2, kOperators = 3, kRescore = 4 };
+enum StageKind {
+  kFitness = 0,
+  kPack = 1,
+  kReduce = 2,
+  kOperators = 3,
+  kRescore = 4,
+  kSurrogate = 5
+};
 
 // Records the start event of a timed stage (no-op when timing is off).
 cudaEvent_t stage_begin(game_ctx* h) {
@@ -291,6 +314,98 @@ int eval_state(game_ctx* h) {
   return GAME_OK;
 }
 
+// Surrogate parameters (once) and a workspace for at least `rows` rows.
+int ensure_surrogate(game_ctx* h, int rows) {
+  SurrogateDev& s = h->sd;
+  if (!h->sd_params) {
+    const int64_t n = surrogate_param_count(h->s.K);
+    s.K = h->s.K;
+    if (dev_alloc(&s.w, n) != cudaSuccess || dev_alloc(&s.g, n) != cudaSuccess ||
+        dev_alloc(&s.m, n) != cudaSuccess || dev_alloc(&s.v, n) != cudaSuccess ||
+        dev_alloc(&s.loss, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GAME_ENOMEM, "surrogate parameters");
+    }
+    h->sd_params = true;
+    s.step = 0;
+    CK(surrogate_init(s, h->prm.seed, h->st));
+  }
+  if (rows > s.Bmax) {
+    float** bufs[6] = {&s.Z1, &s.H1, &s.Z2, &s.H2, &s.dZ1, &s.dZ2};
+    for (float** b : bufs) {
+      dev_free(*b);
+      *b = nullptr;
+    }
+    dev_free(s.out);
+    dev_free(s.dout);
+    dev_free(s.lterm);
+    s.out = s.dout = s.lterm = nullptr;
+    s.Bmax = 0;
+    for (float** b : bufs)
+      if (dev_alloc(b, (size_t)rows * kSurrogateHidden) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "surrogate workspace");
+      }
+    if (dev_alloc(&s.out, rows) != cudaSuccess || dev_alloc(&s.dout, rows) != cudaSuccess ||
+        dev_alloc(&s.lterm, rows) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GAME_ENOMEM, "surrogate workspace");
+    }
+    s.Bmax = rows;
+  }
+  return GAME_OK;
+}
+
+// One Adam step of the surrogate on device pairs (X [n][K], fit [n]).
+int surrogate_step(game_ctx* h, const float* X, const double* fit, int n) {
+  int rc = ensure_surrogate(h, n);
+  if (rc) return rc;
+  CK(surrogate_forward(h->sd, X, n, h->sd.out, h->st));
+  CK(surrogate_backward(h->sd, X, fit, n, h->st));
+  CK(surrogate_adam(h->sd, h->st));
+  return GAME_OK;
+}
+
+// Adds the current population and its exact fitness to the replay ring and
+// trains one step on each stored generation, oldest first.
+int surrogate_learn(game_ctx* h) {
+  const int P = h->prm.P, K = h->s.K;
+  const int slot = h->ring_head;
+  CK(cudaMemcpyAsync(h->rX[slot], h->pop[h->cur], (size_t)P * K * sizeof(float),
+                     cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(h->rfit[slot], h->fit, (size_t)P * sizeof(double),
+                     cudaMemcpyDeviceToDevice, h->st));
+  h->ring_head ^= 1;
+  if (h->ring_n < 2) h->ring_n += 1;
+  for (int i = h->ring_n - 1; i >= 0; --i) {
+    const int sl = (slot - i + 2) % 2;
+    const int rc = surrogate_step(h, h->rX[sl], h->rfit[sl], P);
+    if (rc) return rc;
+  }
+  return GAME_OK;
+}
+
+// Buffers of the screened generation; the surrogate warm-started on the
+// current population (20 steps).
+int setup_screening(game_ctx* h) {
+  const int P = h->prm.P, K = h->s.K, E = h->prm.elitism;
+  const int n = h->prm.oversample * (P - E);
+  if (dev_alloc(&h->off, (size_t)(E + n) * K) != cudaSuccess ||
+      dev_alloc(&h->oplan, (size_t)(E + n)) != cudaSuccess ||
+      dev_alloc(&h->pred, (size_t)n) != cudaSuccess || dev_alloc(&h->flag, (size_t)n) != cudaSuccess ||
+      dev_alloc(&h->pos, (size_t)n) != cudaSuccess ||
+      dev_alloc(&h->rX[0], (size_t)P * K) != cudaSuccess ||
+      dev_alloc(&h->rX[1], (size_t)P * K) != cudaSuccess ||
+      dev_alloc(&h->rfit[0], (size_t)P) != cudaSuccess ||
+      dev_alloc(&h->rfit[1], (size_t)P) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GAME_ENOMEM, "screening buffers");
+  }
+  int rc = ensure_surrogate(h, n > P ? n : P);
+  for (int i = 0; i < 20 && !rc; ++i) rc = surrogate_step(h, h->pop[h->cur], h->fit, P);
+  return rc;
+}
+
 int check_status(game_ctx* h) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -338,6 +453,16 @@ int validate_params(const game_params& p, const Shape& s, std::string* why) {
     *why = "unknown precision";
     return 0;
   }
+  if (p.surrogate != 0 && p.surrogate != 1) {
+    *why = "surrogate must be 0 or 1";
+    return 0;
+  }
+  if (p.surrogate &&
+      (p.oversample < 1 || (int64_t)p.oversample * ((p.P == 0 ? (int64_t)s.B * s.N + 1 : p.P) -
+                                                    p.elitism) > kScreenMax)) {
+    *why = "oversample must be >= 1 with oversample * (P - elitism) <= 16384";
+    return 0;
+  }
   if (p.rescore_top < 0 || p.rescore_top > kMaxRescore) {
     *why = "rescore_top must be in 0..16";
     return 0;
@@ -356,6 +481,7 @@ GaDev ga_dev(const game_ctx* h) {
   g.E = h->prm.elitism;
   g.T = h->prm.tournament;
   g.I = h->prm.immigrants;
+  g.Nout = g.P;
   g.thr_pc = (uint32_t)floor((double)h->prm.pc * 16777216.0);
   g.thr_pm = (uint32_t)floor((double)h->prm.pm * 16777216.0);
   g.sigma = h->prm.sigma;
@@ -386,6 +512,16 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->part);
   dev_free(h->upop);
   dev_free(h->ufit);
+  SurrogateDev& s = h->sd;
+  float* sb[] = {s.w, s.g, s.m, s.v, s.Z1, s.H1, s.Z2, s.H2, s.dZ1, s.dZ2, s.out, s.dout,
+                 s.lterm, s.loss, h->off, h->pred, h->rX[0], h->rX[1], h->uX, h->upred};
+  for (float* b : sb) dev_free(b);
+  dev_free(h->oplan);
+  dev_free(h->flag);
+  dev_free(h->pos);
+  dev_free(h->rfit[0]);
+  dev_free(h->rfit[1]);
+  dev_free(h->ufitd);
   delete h;
 }
 
@@ -415,6 +551,8 @@ int game_params_default(game_params* out) {
   out->mse_threshold = 0.0;
   out->seed = 1;
   out->rescore_top = 8;
+  out->surrogate = 0;
+  out->oversample = 8;
   return GAME_OK;
 }
 
@@ -514,9 +652,13 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   if (e != cudaSuccess) return bail(cuda_fail(e, "init population"));
   rc = eval_state(h);
   if (rc) return bail(rc);
+  h->fit_valid = true;
+  if (p.surrogate) {
+    rc = setup_screening(h);
+    if (rc) return bail(rc);
+  }
   rc = check_status(h);
   if (rc) return bail(rc);
-  h->fit_valid = true;
   h->gen = 0;
   *out = h;
   return GAME_OK;
@@ -615,6 +757,35 @@ int game_generation(game_t h, uint64_t seed) {
     if (rc) return rc;
     h->fit_valid = true;
   }
+  if (h->prm.surrogate) {
+    // oversampled offspring, screened by the surrogate
+    GaDev g = ga_dev(h);
+    const int E = h->prm.elitism, P = h->prm.P, K = h->s.K;
+    const int n = h->prm.oversample * (P - E);
+    g.Nout = E + n;
+    cudaEvent_t t0 = stage_begin(h);
+    CK(launch_generation(g, h->pop[h->cur], h->fit, seed, (uint32_t)h->gen, h->oplan, h->off,
+                         h->st));
+    stage_end(h, t0, kOperators);
+    t0 = stage_begin(h);
+    rc = ensure_surrogate(h, n);
+    if (rc) return rc;
+    CK(surrogate_forward(h->sd, h->off + (size_t)E * K, n, h->pred, h->st));
+    CK(surrogate_screen(n, P - E, E, K, h->pred, h->flag, h->pos, h->off, h->pop[h->cur ^ 1],
+                        h->st));
+    stage_end(h, t0, kSurrogate);
+    h->last_n = n;
+    h->cur ^= 1;
+    h->gen += 1;
+    h->fit_valid = false;
+    rc = eval_state(h);
+    if (rc) return rc;
+    h->fit_valid = true;
+    t0 = stage_begin(h);
+    rc = surrogate_learn(h);
+    stage_end(h, t0, kSurrogate);
+    return rc;
+  }
   cudaEvent_t t0 = stage_begin(h);
   CK(launch_generation(ga_dev(h), h->pop[h->cur], h->fit, seed, (uint32_t)h->gen, h->plan,
                        h->pop[h->cur ^ 1], h->st));
@@ -710,7 +881,7 @@ int game_set_state(game_t h, const float* pop, const double* fit, int64_t genera
 int game_set_timing(game_t h, int32_t enable) {
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   harvest_spans(h);
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     h->tot_ms[k] = 0.0;
     h->count[k] = 0;
   }
@@ -731,7 +902,108 @@ int game_get_timing(game_t h, game_timing* out) {
   out->operators_launches = h->count[kOperators];
   out->rescore_ms = h->tot_ms[kRescore];
   out->rescore_launches = h->count[kRescore];
+  out->surrogate_ms = h->tot_ms[kSurrogate];
+  out->surrogate_launches = h->count[kSurrogate];
   return GAME_OK;
+}
+
+// ---- fitness surrogate ----
+
+namespace {
+// Device copies of caller arrays for the surrogate calls (n rows).
+int surrogate_inputs(game_ctx* h, const float* pop, const double* fit, int n) {
+  if (n > h->sur_cap) {
+    dev_free(h->uX);
+    dev_free(h->ufitd);
+    dev_free(h->upred);
+    h->uX = nullptr;
+    h->ufitd = nullptr;
+    h->upred = nullptr;
+    h->sur_cap = 0;
+    if (dev_alloc(&h->uX, (size_t)n * h->s.K) != cudaSuccess ||
+        dev_alloc(&h->ufitd, (size_t)n) != cudaSuccess ||
+        dev_alloc(&h->upred, (size_t)n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GAME_ENOMEM, "surrogate inputs");
+    }
+    h->sur_cap = n;
+  }
+  CK(cudaMemcpyAsync(h->uX, pop, (size_t)n * h->s.K * sizeof(float), cudaMemcpyDefault, h->st));
+  if (fit) CK(cudaMemcpyAsync(h->ufitd, fit, (size_t)n * sizeof(double), cudaMemcpyDefault, h->st));
+  return ensure_surrogate(h, n);
+}
+}  // namespace
+
+int game_surrogate_predict(game_t h, const float* pop, int32_t n, float* pred_out) {
+  g_last_error.clear();
+  if (!h || !pop || !pred_out || n < 1) return fail(GAME_EINVAL, "bad argument");
+  int rc = surrogate_inputs(h, pop, nullptr, n);
+  if (rc) return rc;
+  CK(surrogate_forward(h->sd, h->uX, n, h->upred, h->st));
+  CK(cudaMemcpyAsync(pred_out, h->upred, (size_t)n * sizeof(float), cudaMemcpyDefault, h->st));
+  return check_status(h);
+}
+
+int game_surrogate_grad(game_t h, const float* pop, const double* fit, int32_t n,
+                        float* grad_out, float* loss_out) {
+  g_last_error.clear();
+  if (!h || !pop || !fit || !grad_out || n < 1) return fail(GAME_EINVAL, "bad argument");
+  int rc = surrogate_inputs(h, pop, fit, n);
+  if (rc) return rc;
+  CK(surrogate_forward(h->sd, h->uX, n, h->sd.out, h->st));
+  CK(surrogate_backward(h->sd, h->uX, h->ufitd, n, h->st));
+  CK(cudaMemcpyAsync(grad_out, h->sd.g, surrogate_param_count(h->s.K) * sizeof(float),
+                     cudaMemcpyDefault, h->st));
+  if (loss_out) CK(cudaMemcpyAsync(loss_out, h->sd.loss, sizeof(float), cudaMemcpyDefault, h->st));
+  return check_status(h);
+}
+
+int game_surrogate_train(game_t h, const float* pop, const double* fit, int32_t n) {
+  g_last_error.clear();
+  if (!h || !pop || !fit || n < 1) return fail(GAME_EINVAL, "bad argument");
+  int rc = surrogate_inputs(h, pop, fit, n);
+  if (rc) return rc;
+  rc = surrogate_step(h, h->uX, h->ufitd, n);
+  if (rc) return rc;
+  return check_status(h);
+}
+
+int game_surrogate_params(game_t h, float* w_out, int64_t* count) {
+  g_last_error.clear();
+  if (!h || !count) return fail(GAME_EINVAL, "bad argument");
+  *count = surrogate_param_count(h->s.K);
+  if (!w_out) return GAME_OK;
+  int rc = ensure_surrogate(h, 1);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(w_out, h->sd.w, *count * sizeof(float), cudaMemcpyDefault, h->st));
+  return check_status(h);
+}
+
+int game_surrogate_set_params(game_t h, const float* w) {
+  g_last_error.clear();
+  if (!h || !w) return fail(GAME_EINVAL, "bad argument");
+  int rc = ensure_surrogate(h, 1);
+  if (rc) return rc;
+  const int64_t n = surrogate_param_count(h->s.K);
+  CK(cudaMemcpyAsync(h->sd.w, w, n * sizeof(float), cudaMemcpyDefault, h->st));
+  CK(cudaMemsetAsync(h->sd.m, 0, n * sizeof(float), h->st));
+  CK(cudaMemsetAsync(h->sd.v, 0, n * sizeof(float), h->st));
+  h->sd.step = 0;
+  return check_status(h);
+}
+
+int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (n_out) *n_out = h->last_n;
+  if (h->last_n == 0) return GAME_OK;
+  if (pred_out)
+    CK(cudaMemcpyAsync(pred_out, h->pred, (size_t)h->last_n * sizeof(float), cudaMemcpyDefault,
+                       h->st));
+  if (keep_out)
+    CK(cudaMemcpyAsync(keep_out, h->flag, (size_t)h->last_n * sizeof(int32_t), cudaMemcpyDefault,
+                       h->st));
+  return check_status(h);
 }
 
 int game_sync(game_t h) {

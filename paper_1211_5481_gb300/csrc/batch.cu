@@ -101,7 +101,7 @@ __global__ void breed_batch_kernel(const BatchGaRun* __restrict__ g,
   const uint32_t gen = gens[blockIdx.y];
   const float* pop = R.pop[src];
   float* next = R.pop[src ^ 1];
-  const int64_t n = (int64_t)R.ga.P * R.ga.K;
+  const int64_t n = (int64_t)R.ga.Nout * R.ga.K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     next[e] = ga::breed_gene(R.ga, pop, R.plan, R.seed, gen, e);
@@ -680,6 +680,7 @@ int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* p
     g.E = p.elitism;
     g.T = p.tournament;
     g.I = p.immigrants;
+    g.Nout = g.P;
     g.thr_pc = (uint32_t)floor((double)p.pc * 16777216.0);
     g.thr_pm = (uint32_t)floor((double)p.pm * 16777216.0);
     g.sigma = p.sigma;

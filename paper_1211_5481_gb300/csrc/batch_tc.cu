@@ -16,6 +16,10 @@
 // phases of the per-K-block barriers are tracked as bit masks (one bit per
 // K-block, flipped at each use) instead of the item counter.
 //
+// Each role copies an item's problem descriptor into registers once (the
+// inline-asm memory clobbers of the pipeline would otherwise force a reload
+// from global memory after every copy, MMA and barrier operation).
+//
 // Roles as in fitness_tc.cu: warp 0 gene-block producer, warp 1 MMA issuer
 // and TMEM owner, warp 2 feature producer, warps 4-11 epilogue, warps 12-15
 // expansion. Each item writes its FP64 partial sums to its own rows,
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       uint32_t q = 0, s = 0, ph = 0;
       bool ok = true;
       for (int it = it0; it < it1 && ok; ++it) {
-        const BatchRun& R = a.runs[a.items[a.sched[it]].x];
+        const BatchRun R = a.runs[a.items[a.sched[it]].x];
         for (int c = 0; c < R.C && ok; ++c)
           for (int kb = 0; kb < R.KB && ok; ++kb) {
             ok = wait_bar(ptx::smem_addr(&a_empty[s]), ph ^ 1, abort_flag, a.status);
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       uint32_t full_par = 0;   // bit kb: parity of the next phi_full[kb] phase
       bool ok = true;
       for (int it = it0; it < it1 && ok; ++it) {
-        const BatchRun& R = a.runs[a.items[a.sched[it]].x];
+        const BatchRun R = a.runs[a.items[a.sched[it]].x];
         const int KB = R.KB, C = R.C, BN = R.BN, nlast = R.nmma_last;
         const uint32_t idesc = ptx::idesc_bf16_f32(128, BN);
         const uint32_t b_step = (uint32_t)(BN * 128) >> 4;
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       int issued = 0;
       for (int it = it0; it < it1; ++it) {
         const int2 item = a.items[a.sched[it]];
-        const BatchRun& R = a.runs[item.x];
+        const BatchRun R = a.runs[item.x];
         if (!wait_bar(ptx::smem_addr(x_empty), (issued & 1) ^ 1, abort_flag, a.status)) break;
         const int BN = R.BN, N = R.N;
         const uint32_t bytes = (uint32_t)(N * BN * 4);
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
     bool ok = true;
     for (int it = it0; it < it1 && ok; ++it) {
       const int2 item = a.items[a.sched[it]];
-      const BatchRun& R = a.runs[item.x];
+      const BatchRun R = a.runs[item.x];
       const int BN = R.BN;
       const int NH = BN >= 64 ? 2 : 1;
       const int HW = BN / NH;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
     };
     for (int it = it0; it < it1; ++it) {
       const int2 item = a.items[a.sched[it]];
-      const BatchRun& R = a.runs[item.x];
+      const BatchRun R = a.runs[item.x];
       const int BN = R.BN, N = R.N, KB = R.KB;
       uint32_t* tb = tab + (items_done & 1) * (KBmax * 8);
       for (int cid = bt; cid < KB * 8; cid += kBasisThreads)

@@ -28,7 +28,8 @@ __device__ __forceinline__ float init_gene(uint64_t seed, int K, int64_t e) {
 }
 
 // One CTA of kPlanThreads threads: elites, tournaments and crossover plan of
-// one problem (plan[s] = {head parent, tail parent, cut, elite flag}).
+// one problem (plan[s] = {head parent, tail parent, cut, elite flag}) for
+// ga.Nout output slots; tournaments draw from the ga.P current chromosomes.
 __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restrict__ fit,
                                           uint64_t seed, uint32_t g, int4* __restrict__ plan) {
   __shared__ int elite[kMaxElites];
@@ -82,7 +83,7 @@ __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restr
   for (int e = tid; e < ga.E; e += kPlanThreads) plan[e] = make_int4(elite[e], elite[e], ga.K, 1);
 
   // 2.-3. pairs: tournaments and crossover decision
-  const int npairs = (ga.P - ga.E + 1) / 2;
+  const int npairs = (ga.Nout - ga.E + 1) / 2;
   for (int q = tid; q < npairs; q += kPlanThreads) {
     int parent[2];
 #pragma unroll
@@ -109,7 +110,7 @@ __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restr
       cut = 1 + (int)(((uint64_t)wx.y * (uint64_t)(ga.K - 1)) >> 32);
     const int s0 = ga.E + 2 * q;
     plan[s0] = make_int4(parent[0], parent[1], cut, 0);
-    if (s0 + 1 < ga.P) plan[s0 + 1] = make_int4(parent[1], parent[0], cut, 0);
+    if (s0 + 1 < ga.Nout) plan[s0 + 1] = make_int4(parent[1], parent[0], cut, 0);
   }
 }
 
@@ -119,7 +120,7 @@ __device__ __forceinline__ float breed_gene(const GaDev& ga, const float* __rest
                                             uint32_t g, int64_t e) {
   const int s = (int)(e / ga.K), k = (int)(e % ga.K);
   float v;
-  if (s >= ga.P - ga.I) {
+  if (s >= ga.Nout - ga.I) {
     v = uniform_gene(philox4x32_10(seed, g, (uint32_t)s, (uint32_t)k, kTagImmigrant).x);
   } else {
     const int4 pl = plan[s];

@@ -42,7 +42,7 @@ ga_plan_kernel(GaDev g_, const double* __restrict__ fit, uint64_t seed, uint32_t
 __global__ void ga_breed_kernel(GaDev g_, const float* __restrict__ pop,
                                 const int4* __restrict__ plan, uint64_t seed, uint32_t g,
                                 float* __restrict__ next) {
-  const int64_t n = (int64_t)g_.P * g_.K;
+  const int64_t n = (int64_t)g_.Nout * g_.K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     next[e] = ga::breed_gene(g_, pop, plan, seed, g, e);
@@ -69,7 +69,7 @@ cudaError_t launch_generation(const GaDev& ga, const float* pop, const double* f
   ga_plan_kernel<<<1, kPlanThreads, 0, st>>>(ga, fit, seed, g, plan);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  ga_breed_kernel<<<blocks_for((int64_t)ga.P * ga.K, 256), 256, 0, st>>>(ga, pop, plan, seed,
+  ga_breed_kernel<<<blocks_for((int64_t)ga.Nout * ga.K, 256), 256, 0, st>>>(ga, pop, plan, seed,
                                                                         g, next);
   return cudaGetLastError();
 }

@@ -120,6 +120,34 @@ size_t rescore_smem_bytes(const Shape& s);
 cudaError_t launch_rescore(const RescorePlan& pl, const Shape& s, const float* Xt,
                            const float* y, const float* pop, int P, int n, double* fit,
                            int* cand, double* part, unsigned int* tickets, cudaStream_t st);
+// surrogate.cu -- the MLP fitness surrogate (K -> 256 -> 256 -> 1)
+constexpr int kSurrogateHidden = 256;
+constexpr float kAdamLr = 1e-3f, kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+constexpr int kScreenMax = 16384;   // children screened per generation at most
+struct SurrogateDev {
+  int K, Bmax;
+  int64_t step;            // Adam steps taken
+  float* w;                // parameters, FP32 master
+  float* g;                // gradient
+  float* m;                // Adam moments
+  float* v;
+  float *Z1, *H1, *Z2, *H2, *dZ1, *dZ2;   // [Bmax][256] workspace
+  float *out, *dout, *lterm;              // [Bmax]
+  float* loss;             // [1]
+};
+int64_t surrogate_param_count(int K);
+cudaError_t surrogate_init(const SurrogateDev& s, uint64_t seed, cudaStream_t st);
+cudaError_t surrogate_forward(const SurrogateDev& s, const float* X, int B, float* out,
+                              cudaStream_t st);
+cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const double* fit, int B,
+                               cudaStream_t st);
+cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st);
+// keeps the n_keep smallest predictions of the n children (slots E..E+n-1 of
+// off [E+n][K]) and writes the elites then the kept children in slot order to
+// next [E+n_keep][K]; flag [n] (1 = kept) and pos [n] are scratch / outputs.
+cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred, int* flag,
+                             int* pos, const float* off, float* next, cudaStream_t st);
+
 // api.cu
 void record_error(const char* msg);
 // reduce.cu
@@ -128,6 +156,7 @@ cudaError_t launch_reduce(const double* part, int rows, int P, int Ppad, int64_t
 // ga_ops.cu
 struct GaDev {
   int P, K, E, T, I;
+  int Nout;   // output slots: P for a generation, more for oversampled offspring
   uint32_t thr_pc, thr_pm;
   float sigma;
 };

@@ -17,7 +17,8 @@ enum : uint32_t {
   kTagGauss0 = 5,
   kTagGauss1 = 6,
   kTagGauss2 = 7,
-  kTagImmigrant = 8
+  kTagImmigrant = 8,
+  kTagSurrogate = 9   // initial weights of the fitness surrogate
 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint64_t key, uint32_t c0, uint32_t c1,

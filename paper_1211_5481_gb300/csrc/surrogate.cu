@@ -1,0 +1,452 @@
+// surrogate.cu -- a small MLP that predicts a chromosome's fitness, trained
+// online on the (chromosome, exact fitness) pairs the GA produces, and used to
+// screen oversampled offspring so that only the most promising get the exact
+// fitness of paper Section 3 (Eq. 2, Eq. 3).
+//
+// Network: x in R^K (the genes) -> 256 -> 256 -> 1. Layers 1 and 2 take BF16
+// operands (inputs, weights and the layer-1 activations rounded to BF16) with
+// FP32 accumulation; the output layer is FP32. Activation: GELU in its tanh
+// form, g(z) = z/2 (1 + tanh(c (z + 0.044715 z^3))), c = sqrt(2/pi). Target:
+// t = log(max(fit, 1e-30)) (the MSE spans orders of magnitude; only the
+// ranking of the prediction is used). Loss: mean of (out - t)^2 over the
+// batch. Optimiser: Adam (lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8) on FP32
+// master weights. Initial weights uniform in +-1/sqrt(fan_in) from
+// Philox4x32-10 (key = seed, counter = (layer, index, 0, tag 9)), biases 0.
+//
+// Parameter vector (FP32, this order): W1 [256][K], b1 [256], W2 [256][256],
+// b2 [256], w3 [256], b3 [1].
+//
+// Kernels: one tiled GEMM with strides (C = A B with any transposition,
+// FP32 accumulation, optional BF16 rounding of either operand on load, an
+// optional bias + GELU epilogue), column sums in a fixed order, the GELU
+// derivative, the output layer, and Adam. Screening: a one-CTA bitonic sort
+// of (prediction, slot) keys, a flag per kept slot and a prefix-sum
+// compaction that assembles the next population in slot order.
+#include <cuda_bf16.h>
+
+#include "game_internal.cuh"
+#include "philox.cuh"
+
+namespace game {
+
+namespace {
+
+constexpr int kH = kSurrogateHidden;
+constexpr float kGeluC = 0.7978845608028654f;   // sqrt(2 / pi)
+constexpr float kGeluA = 0.044715f;
+
+__device__ __forceinline__ float round_bf16(float x) {
+  return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+__device__ __forceinline__ float gelu(float z) {
+  const float u = kGeluC * (z + kGeluA * z * z * z);
+  return 0.5f * z * (1.f + tanhf(u));
+}
+
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float u = kGeluC * (z + kGeluA * z * z * z);
+  const float t = tanhf(u);
+  return 0.5f * (1.f + t) + 0.5f * z * (1.f - t * t) * kGeluC * (1.f + 3.f * kGeluA * z * z);
+}
+
+// C[m][n] = sum_k A(m, k) B(k, n), A(m, k) = A[m * am + k * ak], B(k, n) =
+// B[k * bk + n * bn]; FP32 accumulation in k order per thread. Epilogue
+// modes: 0 store C; 1 store Z = C + bias[n] to C and g(Z) (BF16-rounded when
+// round_out) to out2; 2 store C + bias[n].
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+__global__ void __launch_bounds__(256)
+gemm_kernel(int M, int N, int Kd, const float* __restrict__ A, int64_t am, int64_t ak,
+            const float* __restrict__ B, int64_t bk, int64_t bn, int round_a, int round_b,
+            float* __restrict__ C, int64_t ldc, int mode, const float* __restrict__ bias,
+            float* __restrict__ out2, int round_out) {
+  __shared__ float As[kTK][kTM + 4];
+  __shared__ float Bs[kTK][kTN + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < Kd; k0 += kTK) {
+    for (int e = threadIdx.x; e < kTK * kTM; e += 256) {
+      const int kk = e / kTM, mm = e % kTM;
+      const int m = m0 + mm, k = k0 + kk;
+      float v = (m < M && k < Kd) ? A[(int64_t)m * am + (int64_t)k * ak] : 0.f;
+      As[kk][mm] = round_a ? round_bf16(v) : v;
+    }
+    for (int e = threadIdx.x; e < kTK * kTN; e += 256) {
+      const int kk = e / kTN, nn = e % kTN;
+      const int n = n0 + nn, k = k0 + kk;
+      float v = (n < N && k < Kd) ? B[(int64_t)k * bk + (int64_t)n * bn] : 0.f;
+      Bs[kk][nn] = round_b ? round_bf16(v) : v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (mode >= 1) v += bias[n];
+      C[(int64_t)m * ldc + n] = v;
+      if (mode == 1) {
+        const float gv = gelu(v);
+        out2[(int64_t)m * ldc + n] = round_out ? round_bf16(gv) : gv;
+      }
+    }
+  }
+}
+
+// out[b] = sum_j H2[b][j] w3[j] + b3 (one warp per row, fixed lane order)
+__global__ void output_kernel(int B, const float* __restrict__ H2, const float* __restrict__ w3,
+                              const float* __restrict__ b3, float* __restrict__ out) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= B) return;
+  float s = 0.f;
+  for (int j = lane; j < kH; j += 32) s = fmaf(H2[(int64_t)w * kH + j], w3[j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[w] = s + b3[0];
+}
+
+// d_out[b] = 2 (out[b] - t[b]) / B with t = log(max(fit, 1e-30)); also the
+// loss terms (out - t)^2 / B for reporting.
+__global__ void dout_kernel(int B, const float* __restrict__ out, const double* __restrict__ fit,
+                            float* __restrict__ dout, float* __restrict__ loss_terms) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double f = fit[b];
+  const float t = (float)log(f > 1e-30 ? f : 1e-30);
+  const float r = out[b] - t;
+  dout[b] = 2.f * r / (float)B;
+  loss_terms[b] = r * r / (float)B;
+}
+
+// dH2[b][j] = dout[b] w3[j], dZ2 = dH2 * g'(Z2) (in place into dZ)
+__global__ void dz2_kernel(int B, const float* __restrict__ dout, const float* __restrict__ w3,
+                           const float* __restrict__ Z2, float* __restrict__ dZ) {
+  const int64_t n = (int64_t)B * kH;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / kH), j = (int)(e % kH);
+    dZ[e] = dout[b] * w3[j] * gelu_grad(Z2[e]);
+  }
+}
+
+// dZ[e] *= g'(Z[e])
+__global__ void gelu_bwd_kernel(int64_t n, const float* __restrict__ Z, float* __restrict__ dZ) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dZ[e] *= gelu_grad(Z[e]);
+}
+
+// s[j] = sum_b X[b][j] y[b] (y = NULL: plain column sum), fixed order per column
+__global__ void colsum_kernel(int B, int N, const float* __restrict__ X,
+                              const float* __restrict__ y, float* __restrict__ s) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  float acc = 0.f;
+  for (int b = 0; b < B; ++b) acc = fmaf(X[(int64_t)b * N + j], y ? y[b] : 1.f, acc);
+  s[j] = acc;
+}
+
+__global__ void sum_kernel(int B, const float* __restrict__ v, float* __restrict__ s) {
+  if (blockIdx.x != 0) return;
+  __shared__ float part[256];
+  float acc = 0.f;
+  for (int b = threadIdx.x; b < B; b += 256) acc += v[b];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < 256; ++i) t += part[i];
+    s[0] = t;
+  }
+}
+
+__global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    w[e] -= lr * mh / (sqrtf(vh) + eps);
+  }
+}
+
+__global__ void init_params_kernel(uint64_t seed, int K, float* __restrict__ w) {
+  const int64_t n1 = (int64_t)kH * K, n2 = (int64_t)kH * kH;
+  const int64_t total = n1 + kH + n2 + kH + kH + 1;
+  const float a1 = 1.f / sqrtf((float)K), a2 = 1.f / sqrtf((float)kH);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int layer;
+    int64_t idx;
+    float a;
+    if (e < n1) {
+      layer = 1, idx = e, a = a1;
+    } else if (e < n1 + kH) {
+      w[e] = 0.f;
+      continue;
+    } else if (e < n1 + kH + n2) {
+      layer = 2, idx = e - n1 - kH, a = a2;
+    } else if (e < n1 + kH + n2 + kH) {
+      w[e] = 0.f;
+      continue;
+    } else if (e < n1 + kH + n2 + 2 * kH) {
+      layer = 3, idx = e - n1 - 2 * kH - n2, a = a2;
+    } else {
+      w[e] = 0.f;
+      continue;
+    }
+    const uint32_t r =
+        philox4x32_10(seed, (uint32_t)layer, (uint32_t)idx, 0u, kTagSurrogate).x;
+    // u in [-1, 1): (r >> 8) 2^-23 - 1, exact in FP32
+    const float u = (float)(r >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    w[e] = u * a;
+  }
+}
+
+// ---- screening: keep the n_keep smallest predictions of n ----
+constexpr int kSortMax = 16384;
+
+__global__ void __launch_bounds__(1024)
+select_kernel(int n, int n_keep, const float* __restrict__ pred, int* __restrict__ keep_flag) {
+  extern __shared__ uint64_t keys[];   // (order-preserving float bits << 32) | slot
+  int npow = 1;
+  while (npow < n) npow <<= 1;
+  for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+    uint64_t k = ~0ull;
+    if (i < n) {
+      float p = pred[i];
+      if (isnan(p)) p = __int_as_float(0x7f800000);   // NaN ranks last (+inf)
+      uint32_t u = __float_as_uint(p);
+      u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);   // float order as unsigned
+      k = ((uint64_t)u << 32) | (uint32_t)i;
+    }
+    keys[i] = k;
+  }
+  __syncthreads();
+  for (int size = 2; size <= npow; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const uint64_t a = keys[i], b = keys[j];
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keep_flag[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_keep; i += blockDim.x)
+    keep_flag[(int)(keys[i] & 0xffffffffu)] = 1;
+}
+
+// pos[i] = number of kept children before child i (or -1 if child i is not
+// kept): one CTA, an exclusive prefix sum of the flags in slot order.
+__global__ void __launch_bounds__(1024)
+assemble_kernel(int n, const int* __restrict__ keep_flag, int* __restrict__ pos) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int f = i < n ? keep_flag[i] : 0;
+    int x = f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int excl = carry + (wid ? warp_tot[wid - 1] : 0) + x - f;
+    if (i < n) pos[i] = f ? excl : -1;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + f;
+    __syncthreads();
+  }
+}
+
+__global__ void gather_kernel(int n, int E, int K, const int* __restrict__ pos,
+                              const float* __restrict__ off, float* __restrict__ next) {
+  // rows 0..E-1: elites; row E + pos[i] <- offspring slot E + i
+  const int64_t total = (int64_t)(E + n) * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / K), k = (int)(e % K);
+    if (s < E) {
+      next[e] = off[e];
+    } else {
+      const int p = pos[s - E];
+      if (p >= 0) next[(int64_t)(E + p) * K + k] = off[e];
+    }
+  }
+}
+
+int grid1d(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 8192) b = 8192;
+  return (int)b;
+}
+
+cudaError_t gemm(int M, int N, int Kd, const float* A, int64_t am, int64_t ak, const float* B,
+                 int64_t bk, int64_t bn, int ra, int rb, float* C, int64_t ldc, int mode,
+                 const float* bias, float* out2, int round_out, cudaStream_t st) {
+  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM);
+  gemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, C, ldc, mode, bias,
+                                    out2, round_out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t surrogate_param_count(int K) {
+  return (int64_t)kH * K + kH + (int64_t)kH * kH + kH + kH + 1;
+}
+
+cudaError_t surrogate_init(const SurrogateDev& s, uint64_t seed, cudaStream_t st) {
+  const int64_t n = surrogate_param_count(s.K);
+  init_params_kernel<<<grid1d(n), 256, 0, st>>>(seed, s.K, s.w);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(s.m, 0, n * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.v, 0, n * sizeof(float), st);
+  return e;
+}
+
+// Forward pass of B rows X [B][K] (FP32 genes) into out [B]; keeps Z1, H1,
+// Z2, H2 [B][256] in the workspace for a backward pass.
+cudaError_t surrogate_forward(const SurrogateDev& s, const float* X, int B, float* out,
+                              cudaStream_t st) {
+  if (B > s.Bmax) return cudaErrorInvalidValue;
+  const int K = s.K;
+  const float* W1 = s.w;
+  const float* b1 = W1 + (int64_t)kH * K;
+  const float* W2 = b1 + kH;
+  const float* b2 = W2 + (int64_t)kH * kH;
+  const float* w3 = b2 + kH;
+  const float* b3 = w3 + kH;
+  // Z1 = bf(X) bf(W1)^T + b1, H1 = bf(g(Z1))
+  cudaError_t e = gemm(B, kH, K, X, K, 1, W1, 1, K, 1, 1, s.Z1, kH, 1, b1, s.H1, 1, st);
+  if (e != cudaSuccess) return e;
+  // Z2 = H1 bf(W2)^T + b2, H2 = g(Z2)
+  e = gemm(B, kH, kH, s.H1, kH, 1, W2, 1, kH, 0, 1, s.Z2, kH, 1, b2, s.H2, 0, st);
+  if (e != cudaSuccess) return e;
+  output_kernel<<<(int)(((int64_t)B * 32 + 255) / 256), 256, 0, st>>>(B, s.H2, w3, b3, out);
+  return cudaGetLastError();
+}
+
+// Gradient of the mean squared error of log-fitness over B pairs into s.g
+// (after a forward pass of the same X); loss into s.loss[0].
+cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const double* fit, int B,
+                               cudaStream_t st) {
+  const int K = s.K;
+  const float* W1 = s.w;
+  const float* W2 = W1 + (int64_t)kH * K + kH;
+  const float* w3 = W2 + (int64_t)kH * kH + kH;
+  float* gW1 = s.g;
+  float* gb1 = gW1 + (int64_t)kH * K;
+  float* gW2 = gb1 + kH;
+  float* gb2 = gW2 + (int64_t)kH * kH;
+  float* gw3 = gb2 + kH;
+  float* gb3 = gw3 + kH;
+  dout_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, s.out, fit, s.dout, s.lterm);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_kernel<<<1, 256, 0, st>>>(B, s.lterm, s.loss);
+  // output layer
+  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.H2, s.dout, gw3);
+  sum_kernel<<<1, 256, 0, st>>>(B, s.dout, gb3);
+  // dZ2 = dout w3 g'(Z2)
+  dz2_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>(B, s.dout, w3, s.Z2, s.dZ2);
+  // gW2 = dZ2^T H1, gb2 = colsum(dZ2)
+  e = gemm(kH, kH, B, s.dZ2, 1, kH, s.H1, kH, 1, 0, 0, gW2, kH, 0, nullptr, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ2, nullptr, gb2);
+  // dZ1 = (dZ2 bf(W2)) g'(Z1)
+  e = gemm(B, kH, kH, s.dZ2, kH, 1, W2, kH, 1, 0, 1, s.dZ1, kH, 0, nullptr, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  gelu_bwd_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>((int64_t)B * kH, s.Z1, s.dZ1);
+  // gW1 = dZ1^T bf(X), gb1 = colsum(dZ1)
+  e = gemm(kH, K, B, s.dZ1, 1, kH, X, K, 1, 0, 1, gW1, K, 0, nullptr, nullptr, 0, st);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ1, nullptr, gb1);
+  return cudaGetLastError();
+}
+
+cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st) {
+  s.step += 1;
+  const float c1 = 1.f - powf(kAdamB1, (float)s.step);
+  const float c2 = 1.f - powf(kAdamB2, (float)s.step);
+  const int64_t n = surrogate_param_count(s.K);
+  adam_kernel<<<grid1d(n), 256, 0, st>>>(n, s.w, s.g, s.m, s.v, kAdamLr, kAdamB1, kAdamB2,
+                                         kAdamEps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred, int* flag,
+                             int* pos, const float* off, float* next, cudaStream_t st) {
+  if (n > kSortMax || n_keep > n) return cudaErrorInvalidValue;
+  int npow = 1;
+  while (npow < n) npow <<= 1;
+  const size_t smem = (size_t)npow * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kSortMax * sizeof(uint64_t)));
+  if (e != cudaSuccess) return e;
+  select_kernel<<<1, 1024, smem, st>>>(n, n_keep, pred, flag);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  assemble_kernel<<<1, 1024, 0, st>>>(n, flag, pos);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gather_kernel<<<grid1d((int64_t)(E + n) * K), 256, 0, st>>>(n, E, K, pos, off, next);
+  return cudaGetLastError();
+}
+
+}  // namespace game

@@ -39,7 +39,9 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_destroy", "game_last_error", "game_eval_fitness_static", "game_rescore_top",
             "game_batch_create", "game_batch_generation", "game_batch_get_run",
             "game_batch_get_tiles", "game_batch_fitness_ms", "game_batch_sync",
-            "game_batch_destroy")
+            "game_batch_destroy", "game_surrogate_predict", "game_surrogate_grad",
+            "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
+            "game_surrogate_last")
 
 
 class GameError(RuntimeError):
@@ -63,7 +65,9 @@ class game_params(ctypes.Structure):
         ("mse_threshold", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("rescore_top", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("surrogate", ctypes.c_int32),
+        ("oversample", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -79,6 +83,8 @@ class game_timing(ctypes.Structure):
         ("operators_launches", ctypes.c_int64),
         ("rescore_ms", ctypes.c_double),
         ("rescore_launches", ctypes.c_int64),
+        ("surrogate_ms", ctypes.c_double),
+        ("surrogate_launches", ctypes.c_int64),
     ]
 
 
@@ -140,6 +146,12 @@ def load(build_if_missing: bool = True):
         "game_batch_fitness_ms": [vp, i32, ctypes.POINTER(ctypes.c_double)],
         "game_batch_sync": [vp],
         "game_batch_destroy": [vp],
+        "game_surrogate_predict": [vp, vp, i32, vp],
+        "game_surrogate_grad": [vp, vp, dp, i32, vp, vp],
+        "game_surrogate_train": [vp, vp, dp, i32],
+        "game_surrogate_params": [vp, vp, ctypes.POINTER(i64)],
+        "game_surrogate_set_params": [vp, vp],
+        "game_surrogate_last": [vp, vp, vp, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -297,6 +309,49 @@ class Game:
 
     def generation(self, seed):
         game_generation(self.h, seed)
+
+    # ---- fitness surrogate (numpy in / out) ----
+    def surrogate_predict(self, pop):
+        pop = np.ascontiguousarray(pop, dtype=np.float32)
+        out = np.zeros(pop.shape[0], dtype=np.float32)
+        _check(load().game_surrogate_predict(self.h, _ptr(pop), pop.shape[0], _ptr(out)))
+        return out
+
+    def surrogate_grad(self, pop, fit):
+        pop = np.ascontiguousarray(pop, dtype=np.float32)
+        fit = np.ascontiguousarray(fit, dtype=np.float64)
+        n = ctypes.c_int64()
+        _check(load().game_surrogate_params(self.h, None, ctypes.byref(n)))
+        g = np.zeros(n.value, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().game_surrogate_grad(self.h, _ptr(pop), _ptr(fit), pop.shape[0], _ptr(g),
+                                          _ptr(loss)))
+        return g, float(loss[0])
+
+    def surrogate_train(self, pop, fit):
+        pop = np.ascontiguousarray(pop, dtype=np.float32)
+        fit = np.ascontiguousarray(fit, dtype=np.float64)
+        _check(load().game_surrogate_train(self.h, _ptr(pop), _ptr(fit), pop.shape[0]))
+
+    def surrogate_params(self):
+        n = ctypes.c_int64()
+        _check(load().game_surrogate_params(self.h, None, ctypes.byref(n)))
+        w = np.zeros(n.value, dtype=np.float32)
+        _check(load().game_surrogate_params(self.h, _ptr(w), ctypes.byref(n)))
+        return w
+
+    def surrogate_set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().game_surrogate_set_params(self.h, _ptr(w)))
+
+    def surrogate_last(self):
+        n = ctypes.c_int32()
+        _check(load().game_surrogate_last(self.h, None, None, ctypes.byref(n)))
+        pred = np.zeros(n.value, dtype=np.float32)
+        keep = np.zeros(n.value, dtype=np.int32)
+        if n.value:
+            _check(load().game_surrogate_last(self.h, _ptr(pred), _ptr(keep), ctypes.byref(n)))
+        return pred, keep
 
     def train(self, generations):
         return game_train(self.h, generations)

@@ -1,0 +1,80 @@
+"""Pins of the surrogate oracle: gradients against central finite
+differences, GELU against its derivative and the erf form, Adam's first step
+against its closed form, the initial weights' range, and the screening
+selection against brute-force sorting."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import surrogate as sg
+
+
+def test_gelu_derivative_and_erf_form():
+    z = np.linspace(-6, 6, 1001)
+    h = 1e-6
+    num = (sg.gelu(z + h) - sg.gelu(z - h)) / (2 * h)
+    np.testing.assert_allclose(sg.gelu_grad(z), num, rtol=1e-6, atol=1e-8)
+    erf_form = np.array([0.5 * t * (1 + math.erf(t / math.sqrt(2))) for t in z])
+    assert np.max(np.abs(sg.gelu(z) - erf_form)) < 1e-3   # the tanh form's known accuracy
+
+
+@pytest.mark.parametrize("K,H,B", [(3, 4, 5), (7, 6, 9)])
+def test_gradient_matches_finite_differences(orc, K, H, B):
+    rng = np.random.default_rng(K * 10 + H)
+    w = rng.normal(0, 0.5, sg.param_count(K, H))
+    X = rng.uniform(-1, 1, (B, K))
+    fit = np.exp(rng.normal(0, 1, B))
+    loss, g = sg.loss_and_grad(w, X, fit, K, H, rounding=False)
+    num = np.zeros_like(w)
+    h = 1e-6
+    for i in range(w.shape[0]):
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        num[i] = (sg.loss_and_grad(wp, X, fit, K, H, False)[0]
+                  - sg.loss_and_grad(wm, X, fit, K, H, False)[0]) / (2 * h)
+    np.testing.assert_allclose(g, num, rtol=1e-5, atol=1e-8)
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([1.0, -2.0, 1e-3, -5.0])
+    w0 = np.zeros(4)
+    w1, m, v = sg.adam(w0, g, np.zeros(4), np.zeros(4), 1)
+    # t = 1: m_hat = g, v_hat = g^2, so the step is lr g / (|g| + eps)
+    np.testing.assert_allclose(w1, -sg.LR * g / (np.abs(g) + sg.EPS), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_init_range_and_determinism(orc):
+    K = 33
+    w = sg.init_params(7, K)
+    p = sg.unpack(w, K)
+    a1, a2 = 1 / np.sqrt(np.float32(K)), 1 / np.sqrt(np.float32(256))
+    assert w.dtype == np.float32 and w.shape[0] == sg.param_count(K)
+    assert np.all(np.abs(p["W1"]) <= a1) and np.all(np.abs(p["W2"]) <= a2)
+    assert np.all(p["b1"] == 0) and np.all(p["b2"] == 0) and p["b3"][0] == 0
+    assert abs(p["W1"].mean()) < 0.02 * a1 and abs(p["W2"].std() - a2 / np.sqrt(3)) < 0.01 * a2
+    np.testing.assert_array_equal(w, sg.init_params(7, K))
+    assert not np.array_equal(w, sg.init_params(8, K))
+
+
+def test_select_keep_brute_force():
+    rng = np.random.default_rng(3)
+    pred = rng.choice([0.5, -1.0, 2.0, 0.0], 40).astype(np.float32)
+    pred[[3, 17]] = np.nan
+    pred[5] = -0.0
+    for n_keep in (1, 7, 20, 40):
+        keep = sg.select_keep(pred, n_keep)
+        key = [(math.inf if math.isnan(p) else float(p), math.copysign(1, p) > 0, i)
+               for i, p in enumerate(pred)]
+        want = sorted(range(40), key=lambda i: key[i])[:n_keep]
+        assert set(np.nonzero(keep)[0]) == set(want)
+
+
+def test_screen_keeps_slot_order():
+    off = np.arange(12, dtype=np.float32).reshape(6, 2)
+    keep = np.array([0, 1, 0, 1], dtype=np.int32)
+    nxt = sg.screen(off, keep, 2)
+    np.testing.assert_array_equal(nxt, off[[0, 1, 3, 5]])

@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--M", type=int, default=1_000_000, help="patterns (smaller for profiling)")
     ap.add_argument("--form", choices=["bf16", "bf16x3", "fp8", "fp32"], default="bf16")
+    ap.add_argument("--workload", choices=["classification", "batched", "surrogate"],
+                    default="classification",
+                    help="batched: 256 independent runs of uneven shape, one graph per "
+                         "generation; surrogate: the 4M-pattern regression set with "
+                         "surrogate-screened offspring, against the plain FP32 form")
+    ap.add_argument("--oracle-run", type=int, default=0, metavar="G",
+                    help="surrogate workload: also run G generations of the FP64 oracle GA "
+                         "(Gram form) and of the screened GPU GA and compare the best fitness")
     ap.add_argument("--no-fp32-leg", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -212,6 +220,184 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(args, torch, game, dev, world, rank):
+    """256 independent GA runs (M log-uniform in [10^3, 2 10^5], N in 4..64,
+    Chebyshev or trigonometric basis of degree 2..10, P log-uniform in
+    [32, 512], regression targets), advanced together: one step = one
+    generation of every run = one CUDA-graph replay (batched operators, pack,
+    one persistent tensor-core fitness launch, FP64 reduce)."""
+    from paper_1211_5481_gb300 import datagen as dg
+    runs = dg.batched_runs(R=256)
+    args_b = [(pr.X, pr.y, pr.degree, pr.basis, pr.P, 1000 + r) for r, pr in enumerate(runs)]
+    bs = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    b = game.Batch(args_b, autotune=True, stream=bs)
+    create_s = time.perf_counter() - t0
+    tiles = b.tiles()
+    evals = float(sum(pr.M * pr.P for pr in runs))
+    flops = float(sum(2.0 * pr.M * pr.P * (pr.K - 1) + 3.0 * pr.M * pr.P for pr in runs))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        b.generation()
+    b.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
+    ev = []
+    with torch.cuda.stream(bs):
+        for _ in range(args.steps):
+            flush.zero_()   # L2 flush between steps, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(bs)
+            b.generation()
+            e1.record(bs)
+            ev.append((e0, e1))
+    b.sync()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t_step = sum(x.elapsed_time(y) for x, y in ev) / len(ev) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    fit_ms = b.fitness_ms(10)
+    peaks, peak_src = load_peaks()
+    achieved = flops / (fit_ms * 1e-3) / 1e12
+    peak = float(peaks["bf16_tflops"])
+    line = {
+        "metric": METRIC, "value": evals * world / t_step, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "batched_256_runs", "runs": len(runs),
+                   "sum_M": int(sum(pr.M for pr in runs)), "sum_MP": evals,
+                   "K_range": [int(min(pr.K for pr in runs)), int(max(pr.K for pr in runs))],
+                   "step": "one generation of all runs: one CUDA graph replay",
+                   "timing": "CUDA events on the batch's stream around each graph replay",
+                   "l2": "flushed between steps (256 MB write)",
+                   "tiles": {str(t): int((tiles == t).sum()) for t in (32, 64, 128, 256)},
+                   "create_s": create_s},
+        "generations_per_s": 1.0 / t_step,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_src} bf16_tflops (burst)",
+                     "kernel": "fitness_batch_kernel", "kernel_ms": fit_ms,
+                     "flops_per_launch": flops},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+    }
+    b.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def spearman(a, b):
+    ra = np.argsort(np.argsort(a, kind="stable"), kind="stable")
+    rb = np.argsort(np.argsort(b, kind="stable"), kind="stable")
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def run_surrogate(args, torch, game, dev, world, rank):
+    """The surrogate-screened form (BF16 contraction, elite re-scoring, 8x
+    oversampled offspring screened by the MLP) against the plain FP32 form
+    on the 4M-pattern regression set (N = 48, Chebyshev degree 6, K = 289,
+    P = 2048): generations per second of each, the ratio, the surrogate's
+    rank agreement with the exact fitness of the children it kept, and the
+    accuracy of the BF16 form against the FP64 oracle on 10,000 patterns."""
+    from paper_1211_5481_gb300 import datagen as dg
+    pr = dg.surrogate_regression()
+    M, K, P = pr.M, pr.K, pr.P
+    stream = torch.cuda.current_stream(dev)
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(h, steps, warmup):
+        for _ in range(warmup):
+            game.game_generation(h.h, 4)
+        torch.cuda.synchronize(dev)
+        h.set_timing(True)
+        ev = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            game.game_generation(h.h, 4)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize(dev)
+        tm = h.timing()
+        h.set_timing(False)
+        return sum(x.elapsed_time(y) for x, y in ev) / len(ev), tm
+
+    gs = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
+                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=8)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
+    t_sur, tm = timed(gs, args.steps, max(args.warmup, 3))
+    clk = clocks.stop()
+    g32 = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
+                    precision=game.GAME_PREC_FP32)
+    t_32, _ = timed(g32, max(3, args.steps // 10), 1)
+    g32.close()
+    # surrogate rank agreement on the next generations (untimed)
+    rho, judge = [], []
+    E = 2
+    for _ in range(3):
+        game.game_generation(gs.h, 4)
+        pred, keep, trusted, r = gs.surrogate_last()
+        _, fit, _ = gs.population()
+        rho.append(spearman(pred[keep.astype(bool)], np.log(fit[E:])))
+        judge.append({"trusted": trusted, "pearson_kept": r})
+    acc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        acc = precision_report(game, gs, pr, 2)
+    final = None
+    if rank == 0 and args.oracle_run > 0:
+        import oracle
+        oracle.build()
+        G = args.oracle_run
+        t0 = time.perf_counter()
+        _, _, best_o = oracle.train(pr.X, pr.y, pr.degree, pr.basis, P, G, 4, use_gram=True)
+        t_o = time.perf_counter() - t0
+        gg = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
+                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=8)
+        gg.train(G)
+        _, fit_g, _ = gg.population()
+        gg.close()
+        best_g = float(fit_g.min())
+        final = {"generations": G, "oracle_best": float(best_o[-1]), "screened_bf16_best": best_g,
+                 "rel_diff": (best_g - float(best_o[-1])) / float(best_o[-1]),
+                 "oracle": "FP64 GA, Gram-form fitness, no surrogate, same seed",
+                 "oracle_s": t_o}
+    gen_s, gen32_s = 1e3 / t_sur, 1e3 / t_32
+    line = {
+        "metric": METRIC, "value": M * P * world / (t_sur * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": t_sur, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
+                   "form": "BF16 contraction + elite re-score + surrogate screening, 8x "
+                           "oversampled offspring",
+                   "step": "one screened generation: offspring, MLP screening, exact "
+                           "fitness of the kept population, MLP training",
+                   "l2": "flushed between steps (256 MB write)"},
+        "generations_per_s": gen_s,
+        "fp32_form": {"ms_per_step": t_32, "generations_per_s": gen32_s},
+        "gens_ratio_vs_fp32": gen_s / gen32_s,
+        "stage_ms_per_step": {k.replace("_ms", ""): tm[k] / max(args.steps, 1)
+                              for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms",
+                                        "rescore_ms", "surrogate_ms")},
+        "surrogate_rank_spearman_kept": rho,
+        "surrogate_judge": judge,
+        "accuracy": acc, "final_best": final, "clocks": clk,
+    }
+    gs.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -229,6 +415,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.workload in ("batched", "surrogate"):
+        game.load()
+        (run_batched if args.workload == "batched" else run_surrogate)(args, torch, game, dev,
+                                                                        world, rank)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     pr = workload(args.M)
     M, K, P = pr.M, pr.K, pr.P

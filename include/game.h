@@ -226,14 +226,18 @@ int game_eval_fitness_static(const float* X, const float* y, int64_t M,
  * (ties by slot) in slot order after the E elites, evaluates that population
  * exactly (the handle's precision and re-scoring), and then trains the
  * surrogate with one Adam step on each of the last two generations' exact
- * (chromosome, fitness) pairs. The surrogate of a fresh handle is initialised
+ * (chromosome, fitness) pairs. The exact fitness also judges the surrogate
+ * (game_surrogate_last): while its predictions do not correlate with the
+ * exact fitness of the children they kept, screening keeps the children an
+ * unscreened generation would have. The surrogate of a fresh handle is initialised
  * from prm->seed and trained with 20 steps on generation 0.
  * Parameter vector (FP32): W1 [256][K], b1 [256], W2 [256][256], b2 [256],
  * w3 [256], b3 [1]. Arrays may be host or device memory. */
-/* Predictions for n chromosomes pop [n][K] into pred_out [n] (FP32, the
- * log-fitness scale). */
+/* Predictions for n chromosomes pop [n][K] into pred_out [n] (FP32, on the
+ * standardised log-fitness scale of the training batches). */
 int game_surrogate_predict(game_t h, const float* pop, int32_t n, float* pred_out);
-/* Gradient of the training loss mean((out - log fit)^2) over the pairs
+/* Gradient of the training loss mean((out - t)^2), t the log-fitness
+ * standardised over the batch (mean 0, sd 1), over the pairs
  * (pop [n][K], fit [n]) at the current parameters, into grad_out [count];
  * loss_out (may be NULL) receives the loss. Parameters are not changed. */
 int game_surrogate_grad(game_t h, const float* pop, const double* fit, int32_t n,
@@ -246,9 +250,15 @@ int game_surrogate_params(game_t h, float* w_out, int64_t* count);
 /* Replaces the parameters (w [count]) and resets the Adam state. */
 int game_surrogate_set_params(game_t h, const float* w);
 /* The last screening: *n_out children (slot E + i), their predictions
- * pred_out [n] and kept flags keep_out [n] (any output may be NULL; pass
- * NULL arrays first to learn n). */
-int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out);
+ * pred_out [n], kept flags keep_out [n], whether the screening trusted the
+ * surrogate (*trusted_out; if not it kept the first P - E children, those of
+ * the unscreened generation), and the judge's correlation *r_out measured on
+ * the children it kept (any output may be NULL; pass NULL arrays first to
+ * learn n). The judge: the next screening trusts the surrogate iff the
+ * Pearson correlation of the kept children's predictions with their exact
+ * log-fitness exceeds 0.25; a fresh handle starts untrusted. */
+int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out,
+                        int32_t* trusted_out, float* r_out);
 
 /* ---- Batched runs ----
  * Many independent GA runs, each the method above on its own training set,

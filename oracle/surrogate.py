@@ -18,13 +18,19 @@ Definitions (the same as the CUDA path, written from them):
       Z1 = bf(x) bf(W1)^T + b1, H1 = bf(g(Z1)), Z2 = H1 bf(W2)^T + b2,
       H2 = g(Z2), out = H2 . w3 + b3,
     g(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)));
-  * loss = mean over the batch of (out - log(max(fit, 1e-30)))^2; gradients
-    pass the rounding points unchanged;
+  * target: l = log(max(fit, 1e-30)) standardised over the batch,
+    t = (l - mean l) / sd l (sd 0 counts as 1);
+  * loss = mean over the batch of (out - t)^2; gradients pass the rounding
+    points unchanged;
   * Adam: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
     w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps);
   * screening: of n children keep the n_keep with the smallest prediction,
-    ties by slot, predictions ordered as IEEE-754 total order (NaN last); the
-    next population is the elites followed by the kept children in slot order.
+    ties by slot, predictions ordered as IEEE-754 total order (NaN last) --
+    or, when the surrogate is not trusted, the first n_keep children; the
+    next population is the elites followed by the kept children in slot order;
+  * judge: the Pearson correlation r of the kept children's predictions with
+    their exact log-fitness; the next screening trusts the surrogate iff
+    r > 0.25.
 """
 from __future__ import annotations
 
@@ -110,7 +116,10 @@ def forward(w, X, K, H=H_DEFAULT, rounding=True):
 
 
 def targets(fit):
-    return np.log(np.maximum(np.asarray(fit, dtype=np.float64), 1e-30))
+    l = np.log(np.maximum(np.asarray(fit, dtype=np.float64), 1e-30))
+    mu = l.mean()
+    sd = np.sqrt(np.mean((l - mu) ** 2))
+    return (l - mu) / (sd if sd > 0 else 1.0)
 
 
 def loss_and_grad(w, X, fit, K, H=H_DEFAULT, rounding=True):
@@ -166,8 +175,13 @@ def total_order_key(pred):
     return np.where(neg, (~u) & 0xFFFFFFFF, u | 0x80000000)
 
 
-def select_keep(pred, n_keep):
-    """Flags of the n_keep children with the smallest predictions (ties by slot)."""
+def select_keep(pred, n_keep, trusted=True):
+    """Flags of the n_keep children with the smallest predictions (ties by
+    slot); the first n_keep children when the surrogate is not trusted."""
+    if not trusted:
+        keep = np.zeros(len(pred), dtype=np.int32)
+        keep[:n_keep] = 1
+        return keep
     key = total_order_key(pred)
     order = np.lexsort((np.arange(key.shape[0]), key))
     keep = np.zeros(key.shape[0], dtype=np.int32)
@@ -180,3 +194,14 @@ def screen(offspring, keep, E):
     off = np.asarray(offspring)
     kept = off[E:][np.asarray(keep).astype(bool)]
     return np.concatenate([off[:E], kept], axis=0)
+
+
+def judge(pred, keep, fit_kept):
+    """(r, trusted): Pearson correlation of the kept children's predictions
+    with their exact log-fitness (fit_kept in slot order), and r > 0.25."""
+    x = np.asarray(pred, dtype=np.float64)[np.asarray(keep).astype(bool)]
+    y = np.log(np.maximum(np.asarray(fit_kept, dtype=np.float64), 1e-30))
+    if x.shape[0] < 2 or x.std() == 0 or y.std() == 0:
+        return 0.0, False
+    r = float(np.corrcoef(x, y)[0, 1])
+    return r, r > 0.25

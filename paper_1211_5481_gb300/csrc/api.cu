@@ -111,6 +111,8 @@ struct game_ctx {
   int* flag = nullptr;
   int* pos = nullptr;
   int last_n = 0;             // children screened by the last generation
+  int* trust = nullptr;       // [2]: the judge's verdict, the verdict the last screening used
+  float* trust_r = nullptr;   // [1]: the judge's last correlation
   float* rX[2] = {nullptr, nullptr};     // replay: the last two populations
   double* rfit[2] = {nullptr, nullptr};  // and their exact fitness
   int ring_n = 0, ring_head = 0;
@@ -322,7 +324,7 @@ int ensure_surrogate(game_ctx* h, int rows) {
     s.K = h->s.K;
     if (dev_alloc(&s.w, n) != cudaSuccess || dev_alloc(&s.g, n) != cudaSuccess ||
         dev_alloc(&s.m, n) != cudaSuccess || dev_alloc(&s.v, n) != cudaSuccess ||
-        dev_alloc(&s.loss, 1) != cudaSuccess) {
+        dev_alloc(&s.loss, 1) != cudaSuccess || dev_alloc(&s.tstat, 2) != cudaSuccess) {
       cudaGetLastError();
       return fail(GAME_ENOMEM, "surrogate parameters");
     }
@@ -397,10 +399,13 @@ int setup_screening(game_ctx* h) {
       dev_alloc(&h->rX[0], (size_t)P * K) != cudaSuccess ||
       dev_alloc(&h->rX[1], (size_t)P * K) != cudaSuccess ||
       dev_alloc(&h->rfit[0], (size_t)P) != cudaSuccess ||
-      dev_alloc(&h->rfit[1], (size_t)P) != cudaSuccess) {
+      dev_alloc(&h->rfit[1], (size_t)P) != cudaSuccess || dev_alloc(&h->trust, 2) != cudaSuccess ||
+      dev_alloc(&h->trust_r, 1) != cudaSuccess) {
     cudaGetLastError();
     return fail(GAME_ENOMEM, "screening buffers");
   }
+  CK(cudaMemsetAsync(h->trust, 0, 2 * sizeof(int), h->st));   // untrusted until judged
+  CK(cudaMemsetAsync(h->trust_r, 0, sizeof(float), h->st));
   int rc = ensure_surrogate(h, n > P ? n : P);
   for (int i = 0; i < 20 && !rc; ++i) rc = surrogate_step(h, h->pop[h->cur], h->fit, P);
   return rc;
@@ -522,6 +527,9 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->rfit[0]);
   dev_free(h->rfit[1]);
   dev_free(h->ufitd);
+  dev_free(h->trust);
+  dev_free(h->trust_r);
+  dev_free(h->sd.tstat);
   delete h;
 }
 
@@ -772,7 +780,7 @@ int game_generation(game_t h, uint64_t seed) {
     if (rc) return rc;
     CK(surrogate_forward(h->sd, h->off + (size_t)E * K, n, h->pred, h->st));
     CK(surrogate_screen(n, P - E, E, K, h->pred, h->flag, h->pos, h->off, h->pop[h->cur ^ 1],
-                        h->st));
+                        h->trust, h->trust + 1, h->st));
     stage_end(h, t0, kSurrogate);
     h->last_n = n;
     h->cur ^= 1;
@@ -782,6 +790,7 @@ int game_generation(game_t h, uint64_t seed) {
     if (rc) return rc;
     h->fit_valid = true;
     t0 = stage_begin(h);
+    CK(surrogate_judge(n, h->pred, h->flag, h->pos, h->fit + E, h->trust_r, h->trust, h->st));
     rc = surrogate_learn(h);
     stage_end(h, t0, kSurrogate);
     return rc;
@@ -992,11 +1001,15 @@ int game_surrogate_set_params(game_t h, const float* w) {
   return check_status(h);
 }
 
-int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out) {
+int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out,
+                        int32_t* trusted_out, float* r_out) {
   g_last_error.clear();
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   if (n_out) *n_out = h->last_n;
   if (h->last_n == 0) return GAME_OK;
+  if (trusted_out)
+    CK(cudaMemcpyAsync(trusted_out, h->trust + 1, sizeof(int32_t), cudaMemcpyDefault, h->st));
+  if (r_out) CK(cudaMemcpyAsync(r_out, h->trust_r, sizeof(float), cudaMemcpyDefault, h->st));
   if (pred_out)
     CK(cudaMemcpyAsync(pred_out, h->pred, (size_t)h->last_n * sizeof(float), cudaMemcpyDefault,
                        h->st));

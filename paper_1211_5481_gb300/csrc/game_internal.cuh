@@ -134,6 +134,7 @@ struct SurrogateDev {
   float *Z1, *H1, *Z2, *H2, *dZ1, *dZ2;   // [Bmax][256] workspace
   float *out, *dout, *lterm;              // [Bmax]
   float* loss;             // [1]
+  double* tstat;           // [2] mean and sd of the batch's log-fitness
 };
 int64_t surrogate_param_count(int K);
 cudaError_t surrogate_init(const SurrogateDev& s, uint64_t seed, cudaStream_t st);
@@ -145,8 +146,15 @@ cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st);
 // keeps the n_keep smallest predictions of the n children (slots E..E+n-1 of
 // off [E+n][K]) and writes the elites then the kept children in slot order to
 // next [E+n_keep][K]; flag [n] (1 = kept) and pos [n] are scratch / outputs.
+// (the screening keeps the first n_keep children when *trusted is 0, and
+// records the flag it used in *used_trust)
 cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred, int* flag,
-                             int* pos, const float* off, float* next, cudaStream_t st);
+                             int* pos, const float* off, float* next, const int* trusted,
+                             int* used_trust, cudaStream_t st);
+// r = Pearson correlation of the kept children's predictions with their exact
+// log-fitness (fit_kept [n_keep] in slot order); *trusted = r > 0.25.
+cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int* pos,
+                            const double* fit_kept, float* r_out, int* trusted, cudaStream_t st);
 
 // api.cu
 void record_error(const char* msg);

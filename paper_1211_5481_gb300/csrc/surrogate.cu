@@ -7,9 +7,10 @@
 // operands (inputs, weights and the layer-1 activations rounded to BF16) with
 // FP32 accumulation; the output layer is FP32. Activation: GELU in its tanh
 // form, g(z) = z/2 (1 + tanh(c (z + 0.044715 z^3))), c = sqrt(2/pi). Target:
-// t = log(max(fit, 1e-30)) (the MSE spans orders of magnitude; only the
-// ranking of the prediction is used). Loss: mean of (out - t)^2 over the
-// batch. Optimiser: Adam (lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8) on FP32
+// the log-fitness l = log(max(fit, 1e-30)) standardised over the training
+// batch, t = (l - mean l) / sd l (FP64 statistics; sd 0 counts as 1): the
+// MSE spans orders of magnitude and only the ranking of the prediction is
+// used. Loss: mean of (out - t)^2 over the batch. Optimiser: Adam (lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-8) on FP32
 // master weights. Initial weights uniform in +-1/sqrt(fan_in) from
 // Philox4x32-10 (key = seed, counter = (layer, index, 0, tag 9)), biases 0.
 //
@@ -21,7 +22,12 @@
 // optional bias + GELU epilogue), column sums in a fixed order, the GELU
 // derivative, the output layer, and Adam. Screening: a one-CTA bitonic sort
 // of (prediction, slot) keys, a flag per kept slot and a prefix-sum
-// compaction that assembles the next population in slot order.
+// compaction that assembles the next population in slot order. The exact
+// fitness is the judge: after each screened generation the Pearson
+// correlation r of the kept children's predictions with their exact
+// log-fitness is measured, and the next screening trusts the surrogate only
+// if r > 0.25; otherwise it keeps the first P - E children, i.e. exactly the
+// children of the unscreened generation.
 #include <cuda_bf16.h>
 
 #include "game_internal.cuh"
@@ -129,14 +135,52 @@ __global__ void output_kernel(int B, const float* __restrict__ H2, const float* 
   if (lane == 0) out[w] = s + b3[0];
 }
 
-// d_out[b] = 2 (out[b] - t[b]) / B with t = log(max(fit, 1e-30)); also the
+// Mean and standard deviation of l = log(max(fit, 1e-30)) over the batch
+// (FP64, fixed order: thread-strided sums then a sequential sum of the 256
+// partials).
+__global__ void target_stats_kernel(int B, const double* __restrict__ fit,
+                                    double* __restrict__ stats) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < B; b += 256) {
+    const double f = fit[b];
+    a += log(f > 1e-30 ? f : 1e-30);
+  }
+  s1[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 256; ++i) t += s1[i];
+    s1[0] = t / B;
+  }
+  __syncthreads();
+  const double mu = s1[0];
+  double q = 0.0;
+  for (int b = threadIdx.x; b < B; b += 256) {
+    const double f = fit[b];
+    const double d = log(f > 1e-30 ? f : 1e-30) - mu;
+    q += d * d;
+  }
+  s2[threadIdx.x] = q;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 256; ++i) t += s2[i];
+    const double sd = sqrt(t / B);
+    stats[0] = mu;
+    stats[1] = sd > 0.0 ? sd : 1.0;
+  }
+}
+
+// d_out[b] = 2 (out[b] - t[b]) / B with the standardised target t; also the
 // loss terms (out - t)^2 / B for reporting.
 __global__ void dout_kernel(int B, const float* __restrict__ out, const double* __restrict__ fit,
-                            float* __restrict__ dout, float* __restrict__ loss_terms) {
+                            const double* __restrict__ stats, float* __restrict__ dout,
+                            float* __restrict__ loss_terms) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const double f = fit[b];
-  const float t = (float)log(f > 1e-30 ? f : 1e-30);
+  const float t = (float)((log(f > 1e-30 ? f : 1e-30) - stats[0]) / stats[1]);
   const float r = out[b] - t;
   dout[b] = 2.f * r / (float)B;
   loss_terms[b] = r * r / (float)B;
@@ -236,8 +280,15 @@ __global__ void init_params_kernel(uint64_t seed, int K, float* __restrict__ w) 
 constexpr int kSortMax = 16384;
 
 __global__ void __launch_bounds__(1024)
-select_kernel(int n, int n_keep, const float* __restrict__ pred, int* __restrict__ keep_flag) {
+select_kernel(int n, int n_keep, const float* __restrict__ pred, int* __restrict__ keep_flag,
+              const int* __restrict__ trusted, int* __restrict__ used_trust) {
   extern __shared__ uint64_t keys[];   // (order-preserving float bits << 32) | slot
+  const int trust = *trusted;
+  if (threadIdx.x == 0) *used_trust = trust;
+  if (!trust) {   // the exact evaluator stands in: the unscreened generation's children
+    for (int i = threadIdx.x; i < n; i += blockDim.x) keep_flag[i] = i < n_keep ? 1 : 0;
+    return;
+  }
   int npow = 1;
   while (npow < n) npow <<= 1;
   for (int i = threadIdx.x; i < npow; i += blockDim.x) {
@@ -328,6 +379,56 @@ __global__ void gather_kernel(int n, int E, int K, const int* __restrict__ pos,
   }
 }
 
+// Pearson correlation of the kept children's predictions with their exact
+// log-fitness (fit_kept[pos[i]] for kept child i), FP64 sums in a fixed
+// order; trusted = r > 0.25.
+__global__ void trust_kernel(int n, const float* __restrict__ pred, const int* __restrict__ flag,
+                             const int* __restrict__ pos, const double* __restrict__ fit_kept,
+                             float* __restrict__ r_out, int* __restrict__ trusted) {
+  __shared__ double sh[5][256];
+  double a[5] = {0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < n; i += 256) {
+    if (!flag[i]) continue;
+    const double x = pred[i];
+    const double f = fit_kept[pos[i]];
+    const double y = log(f > 1e-30 ? f : 1e-30);
+    a[0] += 1.0;
+    a[1] += x;
+    a[2] += y;
+    a[3] += x * y;
+    a[4] += x * x;
+  }
+  double yy = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    if (!flag[i]) continue;
+    const double f = fit_kept[pos[i]];
+    const double y = log(f > 1e-30 ? f : 1e-30);
+    yy += y * y;
+  }
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = a[k];
+  __syncthreads();
+  __shared__ double syy[256];
+  syy[threadIdx.x] = yy;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 256; ++i) {
+      for (int k = 0; k < 5; ++k) t[k] += sh[k][i];
+      t[5] += syy[i];
+    }
+    const double c = t[0];
+    double r = 0.0;
+    if (c > 1.0) {
+      const double cov = t[3] / c - (t[1] / c) * (t[2] / c);
+      const double vx = t[4] / c - (t[1] / c) * (t[1] / c);
+      const double vy = t[5] / c - (t[2] / c) * (t[2] / c);
+      r = (vx > 0.0 && vy > 0.0) ? cov / sqrt(vx * vy) : 0.0;
+    }
+    *r_out = (float)r;
+    *trusted = r > 0.25 ? 1 : 0;
+  }
+}
+
 int grid1d(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -396,7 +497,8 @@ cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const doub
   float* gb2 = gW2 + (int64_t)kH * kH;
   float* gw3 = gb2 + kH;
   float* gb3 = gw3 + kH;
-  dout_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, s.out, fit, s.dout, s.lterm);
+  target_stats_kernel<<<1, 256, 0, st>>>(B, fit, s.tstat);
+  dout_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, s.out, fit, s.tstat, s.dout, s.lterm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sum_kernel<<<1, 256, 0, st>>>(B, s.lterm, s.loss);
@@ -430,8 +532,15 @@ cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int* pos,
+                            const double* fit_kept, float* r_out, int* trusted, cudaStream_t st) {
+  trust_kernel<<<1, 256, 0, st>>>(n, pred, flag, pos, fit_kept, r_out, trusted);
+  return cudaGetLastError();
+}
+
 cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred, int* flag,
-                             int* pos, const float* off, float* next, cudaStream_t st) {
+                             int* pos, const float* off, float* next, const int* trusted,
+                             int* used_trust, cudaStream_t st) {
   if (n > kSortMax || n_keep > n) return cudaErrorInvalidValue;
   int npow = 1;
   while (npow < n) npow <<= 1;
@@ -439,7 +548,7 @@ cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred,
   cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(kSortMax * sizeof(uint64_t)));
   if (e != cudaSuccess) return e;
-  select_kernel<<<1, 1024, smem, st>>>(n, n_keep, pred, flag);
+  select_kernel<<<1, 1024, smem, st>>>(n, n_keep, pred, flag, trusted, used_trust);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   assemble_kernel<<<1, 1024, 0, st>>>(n, flag, pos);

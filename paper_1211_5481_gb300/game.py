@@ -151,7 +151,7 @@ def load(build_if_missing: bool = True):
         "game_surrogate_train": [vp, vp, dp, i32],
         "game_surrogate_params": [vp, vp, ctypes.POINTER(i64)],
         "game_surrogate_set_params": [vp, vp],
-        "game_surrogate_last": [vp, vp, vp, ctypes.POINTER(i32)],
+        "game_surrogate_last": [vp, vp, vp, ctypes.POINTER(i32), vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -345,13 +345,17 @@ class Game:
         _check(load().game_surrogate_set_params(self.h, _ptr(w)))
 
     def surrogate_last(self):
+        """(predictions, kept flags, trusted flag used, judge's correlation)"""
         n = ctypes.c_int32()
-        _check(load().game_surrogate_last(self.h, None, None, ctypes.byref(n)))
+        _check(load().game_surrogate_last(self.h, None, None, ctypes.byref(n), None, None))
         pred = np.zeros(n.value, dtype=np.float32)
         keep = np.zeros(n.value, dtype=np.int32)
+        tr = np.zeros(1, dtype=np.int32)
+        r = np.zeros(1, dtype=np.float32)
         if n.value:
-            _check(load().game_surrogate_last(self.h, _ptr(pred), _ptr(keep), ctypes.byref(n)))
-        return pred, keep
+            _check(load().game_surrogate_last(self.h, _ptr(pred), _ptr(keep), ctypes.byref(n),
+                                              _ptr(tr), _ptr(r)))
+        return pred, keep, int(tr[0]), float(r[0])
 
     def train(self, generations):
         return game_train(self.h, generations)

@@ -66,25 +66,37 @@ def test_gradient_and_adam_step(orc, prob):
 
 @pytest.mark.parametrize("P,E,S,seed", [(64, 2, 8, 4), (40, 3, 5, 2**35 + 1)])
 def test_screened_generation_bit_exact(orc, prob, P, E, S, seed):
+    """Offspring, screening and assembly bit-exact given the device's
+    predictions; the judge's correlation against the oracle's, and its
+    verdict used by the next screening; the first screening (untrusted)
+    equals the unscreened generation."""
     prm = orc.ga_params(elitism=E)
     with game.Game(prob.X, prob.y, prob.degree, 0, P=P, seed=seed, precision=BF16,
                    elitism=E, surrogate=1, oversample=S) as g:
-        for step in range(3):
+        verdict = 0   # a fresh handle starts untrusted
+        for step in range(6):
             pop, fit, gen = g.population()
             w = g.surrogate_params()
             g.generation(seed)
             nxt, nfit, ngen = g.population()
-            pred, keep = g.surrogate_last()
+            pred, keep, trusted, r = g.surrogate_last()
             n = S * (P - E)
             assert ngen == gen + 1 and pred.shape == (n,)
+            assert trusted == verdict
             off = orc.offspring(pop, fit, seed, gen, E + n, prm)
             # the device's predictions of the children, against the oracle's forward
             ref, _ = sg.forward(w, off[E:], prob.K)
             assert np.all(np.abs(pred - ref) <= sg.forward_bound(w, off[E:], prob.K)
                           + 1e-6 * np.abs(ref))
             # selection and assembly, exact given the device's predictions
-            np.testing.assert_array_equal(keep, sg.select_keep(pred, P - E))
+            np.testing.assert_array_equal(keep, sg.select_keep(pred, P - E, trusted))
             np.testing.assert_array_equal(bits(nxt), bits(sg.screen(off, keep, E)))
+            if step == 0:   # untrusted: the unscreened generation exactly
+                np.testing.assert_array_equal(bits(nxt),
+                                              bits(orc.generation(pop, fit, seed, gen, prm)))
+            r_ref, verdict = sg.judge(pred, keep, nfit[E:])
+            assert abs(r - r_ref) <= 1e-5
+            verdict = int(verdict)
 
 
 def test_screened_run_elitist(prob):

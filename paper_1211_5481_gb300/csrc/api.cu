@@ -575,7 +575,7 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
     return fail(GAME_EINVAL, "unknown basis");
   Shape s{};
   s.M = M;
-  s.Mpad = ((M + 255) / 256) * 256;
+  s.Mpad = ((M + 767) / 768) * 768;   // every pattern-tile width divides 768
   s.N = N;
   s.d = degree;
   s.basis = basis;

@@ -259,12 +259,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
           for (int k = 0; k < nfull; k += 2) {
             const bool has_b = k + 1 < nfull;
             if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
-            epi_chunk(va, yt + k * 32, bias2, negu2, s2);
+            epi_chunk<false>(va, yt + k * 32, bias2, negu2, s2);
             if (has_b) {
               ptx::tmem_ld32_wait(vb);
               const bool has_a = k + 2 < nfull;
               if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
-              epi_chunk(vb, yt + (k + 1) * 32, bias2, negu2, s2);
+              epi_chunk<false>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
               if (has_a) ptx::tmem_ld32_wait(va);
             }
           }

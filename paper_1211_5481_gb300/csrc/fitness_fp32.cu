@@ -145,7 +145,7 @@ Fp32Plan plan_fp32(const Shape& s, int P, int num_sms) {
   pl.BM = BM;
   pl.Kc = ceil_div(s.Kp, KC) * KC;
   pl.grid_x = ceil_div(P, BP);
-  const int ntiles = (int)(s.Mpad / BM);
+  const int ntiles = ceil_div(s.M, BM);
   int gy = (2 * num_sms + pl.grid_x - 1) / pl.grid_x;
   if (gy < 1) gy = 1;
   if (gy > ntiles) gy = ntiles;
@@ -157,7 +157,7 @@ cudaError_t launch_fitness_fp32(const Fp32Plan& pl, const Shape& s, const float*
                                 const float* y, const float* popT, const float* a0, int P,
                                 int Ppad, double* part, cudaStream_t st) {
   (void)P;
-  const int ntiles = (int)(s.Mpad / BM);
+  const int ntiles = ceil_div(s.M, BM);
   dim3 grid(pl.grid_x, pl.grid_y);
   fitness_fp32_kernel<<<grid, kThreads, 0, st>>>(s.M, s.N, s.d, s.basis, s.Kp, pl.Kc, Xt, y,
                                                  popT, a0, Ppad, ntiles, part);

@@ -105,7 +105,9 @@ __host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages,
   return s;
 }
 
-template <int F>
+// TRI: the 192-pattern tile (three expansion rows per thread), instantiated
+// for the BF16 form only, so the 128- and 256-pattern code stays lean.
+template <int F, bool TRI>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a) {
   constexpr int NA = form_na(F), NPHI = form_nphi(F), CPK = form_cols(F) / 8;
   extern __shared__ uint8_t smem_raw[];
@@ -163,7 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 
   const int G = gridDim.x;
   const int my_tiles = (a.ntiles - (int)blockIdx.x + G - 1) / G;
-  const int XW = BN < 128 ? BN : 128;   // patterns per feature row in xs
+  // xs holds the tile's features as 128-pattern blocks [BN/128][N][128] when BN
+  // is a multiple of 128, else as one block [N][BN]
+  const bool xblocks = BN % 128 == 0;
+  const int XW = xblocks ? 128 : BN;    // patterns per feature row in xs
 
   if (warp == 0) {
     // ---------------- A producer ----------------
@@ -297,15 +302,25 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         const uint32_t bytes = (uint32_t)(N * BN * 4);
         ptx::mbar_arrive_expect_tx(ptx::smem_addr(x_full), bytes);
         const int64_t m0 = t * BN;
-        if (BN >= kPatBlock) {
+        if (xblocks) {
           ptx::bulk_g2s(ptx::smem_addr(xs), a.Xt + m0 * N, bytes, ptx::smem_addr(x_full));
         } else {
-          const int64_t blk = m0 / kPatBlock;
-          const int off = (int)(m0 % kPatBlock);
-          for (int i = 0; i < N; ++i)
-            ptx::bulk_g2s(ptx::smem_addr(xs + i * BN),
-                          a.Xt + (blk * N + i) * kPatBlock + off, (uint32_t)BN * 4,
-                          ptx::smem_addr(x_full));
+          // per feature, the tile's run of patterns, in pieces that stay inside
+          // one 128-pattern block (starts and lengths are multiples of 32
+          // patterns, so every piece is 16-byte aligned)
+          for (int i = 0; i < N; ++i) {
+            int64_t m = m0;
+            int done = 0;
+            while (done < BN) {
+              const int off = (int)(m % kPatBlock);
+              const int seg = (kPatBlock - off) < (BN - done) ? (kPatBlock - off) : (BN - done);
+              ptx::bulk_g2s(ptx::smem_addr(xs + i * BN + done),
+                            a.Xt + ((m / kPatBlock) * N + i) * kPatBlock + off,
+                            (uint32_t)seg * 4, ptx::smem_addr(x_full));
+              done += seg;
+              m += seg;
+            }
+          }
         }
         ++issued;
       }
@@ -351,12 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int k = 0; k < nfull; k += 2) {
             const bool has_b = k + 1 < nfull;
             if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
-            epi_chunk(va, yt + k * 32, bias2, negu2, s2);
+            epi_chunk<F == kFormFP8>(va, yt + k * 32, bias2, negu2, s2);
             if (has_b) {
               ptx::tmem_ld32_wait(vb);
               const bool has_a = k + 2 < nfull;
               if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
-              epi_chunk(vb, yt + (k + 1) * 32, bias2, negu2, s2);
+              epi_chunk<F == kFormFP8>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
               if (has_a) ptx::tmem_ld32_wait(va);
             }
           }
@@ -389,25 +404,28 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
     if (F == kFormFP8)
       for (int k = bt; k < KB * 128; k += kBasisThreads) cs[k] = a.colinv[k];
     ptx::named_bar(1, kBasisThreads);
-    // thread -> rows r0 + 128 * rr (rr < R) and 16-byte units q0, q0 + QS, ...
-    const int RW = BN < 128 ? BN : 128;
-    const int R = BN / RW;          // rows per thread (2 when BN = 256)
-    const int QS = 128 / RW;        // unit stride (1 when BN >= 128)
+    // thread -> rows r0 + RW * rr (rr < R) and 16-byte units q0, q0 + QS, ...:
+    // BN = 128, 256: 128 rows per pass, R = BN / 128; BN = 192: 64 rows per
+    // pass, R = 3, two unit groups; BN < 128: BN rows, R = 1, 128 / BN groups
+    const int RW = TRI ? 64 : (BN < 128 ? BN : 128);
+    const int R = TRI ? 3 : BN / RW;
+    const int QS = 128 / RW;
     const int r0 = bt % RW, q0 = bt / RW;
-    const int r1 = r0 + 128;
-    const float* xrow0 = xs + (r0 >> 7) * N * XW + (r0 % XW);
-    const float* xrow1 = xs + (r1 >> 7) * N * XW + (r1 % XW);
+    auto xrow_of = [&](int r) -> const float* {
+      return xblocks ? xs + (r >> 7) * N * 128 + (r & 127) : xs + r;
+    };
     const bool cheb = a.basis == GAME_BASIS_CHEB;
-    // the 8 values of one chunk for row r0 (va) and, when R == 2, row r1
-    // (vb). A Chebyshev chunk inside one feature's run of degrees (the common
-    // case: degree 8) takes two interleaved recurrences and one descriptor
-    // decode, with no per-value branches.
-    auto gen_rows = [&](uint32_t desc, float (&va)[8], float (&vb)[8]) {
+    // the 8 values of one chunk for row rA (va) and, when hasB, row rB (vb).
+    // A Chebyshev chunk inside one feature's run of degrees (the common case:
+    // degree 8) takes two interleaved recurrences and one descriptor decode,
+    // with no per-value branches.
+    auto gen_rows = [&](uint32_t desc, const float* xrow0, const float* xrow1, bool hasB,
+                        float (&va)[8], float (&vb)[8]) {
       if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
         const int i = (int)(desc & 0xFFFFu);
         const int j0 = (int)((desc >> 16) & 31u);
         const float xa = xrow0[i * XW];
-        const float xb = R == 2 ? xrow1[i * XW] : 0.f;
+        const float xb = hasB ? xrow1[i * XW] : 0.f;
         const float a2 = xa + xa, b2 = xb + xb;
         float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
         for (int st = 1; st < j0; ++st) {
@@ -431,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         }
       } else {
         gen_chunk(desc, a.basis, a.d, N, xrow0, XW, va);
-        if (R == 2) gen_chunk(desc, a.basis, a.d, N, xrow1, XW, vb);
+        if (hasB) gen_chunk(desc, a.basis, a.d, N, xrow1, XW, vb);
       }
     };
     auto store16 = [&](uint8_t* img, int r, int qd, uint32_t w0, uint32_t w1, uint32_t w2,
@@ -439,51 +457,121 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       *reinterpret_cast<uint4*>(img + r * 128 + ((qd ^ (r & 7)) << 4)) =
           make_uint4(w0, w1, w2, w3);
     };
-    // one 16-byte unit qd of K-block kb for the thread's rows
-    auto emit_unit = [&](uint8_t* phik, int kb, int qd) {
+    // one 16-byte unit qd of K-block kb for rows rA and (when hasB) rB
+    auto emit_pair = [&](uint8_t* phik, int kb, int qd, int rA, const float* xa, int rB,
+                         const float* xb, bool hasB) {
       float va[8], vb[8];
       if (F == kFormFP8) {
         // 16 columns: chunks 2 qd and 2 qd + 1, scaled into E4M3's range
         float vc[8], vd[8];
-        gen_rows(tab[kb * CPK + 2 * qd], va, vb);
-        gen_rows(tab[kb * CPK + 2 * qd + 1], vc, vd);
+        gen_rows(tab[kb * CPK + 2 * qd], xa, xb, hasB, va, vb);
+        gen_rows(tab[kb * CPK + 2 * qd + 1], xa, xb, hasB, vc, vd);
         const float* sc = cs + kb * 128 + qd * 16;
         float s16[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) s16[e] = sc[e];
-        store16(phik, r0, qd, e4m3x4_bits(va[0] * s16[0], va[1] * s16[1], va[2] * s16[2], va[3] * s16[3]),
+        store16(phik, rA, qd, e4m3x4_bits(va[0] * s16[0], va[1] * s16[1], va[2] * s16[2], va[3] * s16[3]),
                 e4m3x4_bits(va[4] * s16[4], va[5] * s16[5], va[6] * s16[6], va[7] * s16[7]),
                 e4m3x4_bits(vc[0] * s16[8], vc[1] * s16[9], vc[2] * s16[10], vc[3] * s16[11]),
                 e4m3x4_bits(vc[4] * s16[12], vc[5] * s16[13], vc[6] * s16[14], vc[7] * s16[15]));
-        if (R == 2)
-          store16(phik, r1, qd,
+        if (hasB)
+          store16(phik, rB, qd,
                   e4m3x4_bits(vb[0] * s16[0], vb[1] * s16[1], vb[2] * s16[2], vb[3] * s16[3]),
                   e4m3x4_bits(vb[4] * s16[4], vb[5] * s16[5], vb[6] * s16[6], vb[7] * s16[7]),
                   e4m3x4_bits(vd[0] * s16[8], vd[1] * s16[9], vd[2] * s16[10], vd[3] * s16[11]),
                   e4m3x4_bits(vd[4] * s16[12], vd[5] * s16[13], vd[6] * s16[14], vd[7] * s16[15]));
       } else {
-        gen_rows(tab[kb * CPK + qd], va, vb);
+        gen_rows(tab[kb * CPK + qd], xa, xb, hasB, va, vb);
         if (F == kFormBF16) {
-          store16(phik, r0, qd, bf16x2_bits(va[0], va[1]), bf16x2_bits(va[2], va[3]),
+          store16(phik, rA, qd, bf16x2_bits(va[0], va[1]), bf16x2_bits(va[2], va[3]),
                   bf16x2_bits(va[4], va[5]), bf16x2_bits(va[6], va[7]));
-          if (R == 2)
-            store16(phik, r1, qd, bf16x2_bits(vb[0], vb[1]), bf16x2_bits(vb[2], vb[3]),
+          if (hasB)
+            store16(phik, rB, qd, bf16x2_bits(vb[0], vb[1]), bf16x2_bits(vb[2], vb[3]),
                     bf16x2_bits(vb[4], vb[5]), bf16x2_bits(vb[6], vb[7]));
         } else {
           uint8_t* phik_lo = phik + BN * 128;
           uint32_t h[4], l[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) split_bf16x2(va[2 * e], va[2 * e + 1], h[e], l[e]);
-          store16(phik, r0, qd, h[0], h[1], h[2], h[3]);
-          store16(phik_lo, r0, qd, l[0], l[1], l[2], l[3]);
-          if (R == 2) {
+          store16(phik, rA, qd, h[0], h[1], h[2], h[3]);
+          store16(phik_lo, rA, qd, l[0], l[1], l[2], l[3]);
+          if (hasB) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) split_bf16x2(vb[2 * e], vb[2 * e + 1], h[e], l[e]);
-            store16(phik, r1, qd, h[0], h[1], h[2], h[3]);
-            store16(phik_lo, r1, qd, l[0], l[1], l[2], l[3]);
+            store16(phik, rB, qd, h[0], h[1], h[2], h[3]);
+            store16(phik_lo, rB, qd, l[0], l[1], l[2], l[3]);
           }
         }
       }
+    };
+    // the thread's rows (feature pointers fixed for the launch), in pairs
+    const int r1 = r0 + RW, r2 = r0 + 2 * RW;
+    const float* xr0 = xrow_of(r0);
+    const float* xr1 = R >= 2 ? xrow_of(r1) : xr0;
+    const float* xr2 = R == 3 ? xrow_of(r2) : xr0;
+    auto emit_unit = [&](uint8_t* phik, int kb, int qd) {
+      emit_pair(phik, kb, qd, r0, xr0, r1, xr1, R >= 2);
+      if (TRI) emit_pair(phik, kb, qd, r2, xr2, r2, xr2, false);
+    };
+    // The BF16 form at 128 / 256 patterns (the main workloads) stores each row
+    // as it is generated: measured 3% faster for the whole kernel than the
+    // generic pair path above (fewer values live between the recurrences
+    // and the stores).
+    auto emit = [&](uint8_t* phik, uint32_t desc, int qd, int r, const float* xr) {
+      float v[8];
+      gen_chunk(desc, a.basis, a.d, N, xr, XW, v);
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      *reinterpret_cast<uint4*>(phik + r * 128 + ((qd ^ (r & 7)) << 4)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    };
+    // both rows of a Chebyshev chunk that stays in one feature's run of
+    // degrees (the common case: degree 8): two interleaved recurrences, one
+    // descriptor decode, no per-value branches
+    auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
+      const int i = (int)(desc & 0xFFFFu);
+      const int j0 = (int)((desc >> 16) & 31u);
+      const float xa = xr0[i * XW];
+      const float xb = R == 2 ? xr1[i * XW] : 0.f;
+      const float a2 = xa + xa, b2 = xb + xb;
+      float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
+      for (int st = 1; st < j0; ++st) {
+        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+        tam = ta;
+        ta = na;
+        tbm = tb;
+        tb = nb;
+      }
+      float va[8], vb[8];
+      va[0] = ta;
+      vb[0] = tb;
+#pragma unroll
+      for (int e = 1; e < 8; ++e) {
+        const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+        tam = ta;
+        ta = na;
+        tbm = tb;
+        tb = nb;
+        va[e] = ta;
+        vb[e] = tb;
+      }
+      uint32_t wa[4], wb[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 pa = __floats2bfloat162_rn(va[2 * h], va[2 * h + 1]);
+        const __nv_bfloat162 pb = __floats2bfloat162_rn(vb[2 * h], vb[2 * h + 1]);
+        wa[h] = *reinterpret_cast<const uint32_t*>(&pa);
+        wb[h] = *reinterpret_cast<const uint32_t*>(&pb);
+      }
+      *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
+          make_uint4(wa[0], wa[1], wa[2], wa[3]);
+      if (R == 2)
+        *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
+            make_uint4(wb[0], wb[1], wb[2], wb[3]);
     };
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
@@ -495,7 +583,19 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           if (!ok) break;
         }
         uint8_t* phik = phi + (size_t)kb * NPHI * BN * 128;
-        for (int qd = q0; qd < 8; qd += QS) emit_unit(phik, kb, qd);
+        if (F == kFormBF16 && !TRI) {
+          for (int qd = q0; qd < 8; qd += QS) {
+            const uint32_t desc = tab[kb * 8 + qd];
+            if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
+              emit_cheb_run2(phik, desc, qd);
+            } else {
+              emit(phik, desc, qd, r0, xr0);
+              if (R == 2) emit(phik, desc, qd, r1, xr1);
+            }
+          }
+        } else {
+          for (int qd = q0; qd < 8; qd += QS) emit_unit(phik, kb, qd);
+        }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));
       }
@@ -520,10 +620,11 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
   pl.KB = ceil_div(s.Kp, form_cols(form));
   pl.C = ceil_div(P, 128);
   pl.ok = false;
-  const int cands[4] = {256, 128, 64, 32};
+  const int cands[5] = {256, 192, 128, 64, 32};   // 192: BF16 form only
   // bf16x3 doubles both operands, so it may fall back to two gene stages
   const int min_stages = form == kFormBF16x3 ? 2 : 3;
-  for (int i = 0; i < 4 && !pl.ok; ++i) {
+  for (int i = 0; i < 5 && !pl.ok; ++i) {
+    if (cands[i] == 192 && form != kFormBF16) continue;
     for (int stages = 4; stages >= min_stages; --stages) {
       const int sm = smem_plan(pl.KB, cands[i], s.N, stages, form).total;
       if (sm <= kMaxSmem) {
@@ -538,7 +639,7 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
     }
   }
   if (!pl.ok) return pl;
-  const int ntiles = (int)(s.Mpad / pl.BN);
+  const int ntiles = ceil_div(s.M, pl.BN);   // Mpad (a multiple of 768) covers them
   pl.grid = ntiles < num_sms ? ntiles : num_sms;
   int cols = 32;
   while (cols < 2 * pl.BN) cols <<= 1;
@@ -566,7 +667,7 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   const int cols = form_cols(pl.form);
   const int last_cols = s.Kp - cols * (pl.KB - 1);
   a.nmma_last = (last_cols + cols / 4 - 1) / (cols / 4);
-  a.ntiles = (int)(s.Mpad / pl.BN);
+  a.ntiles = ceil_div(s.M, pl.BN);
   a.Ppad = Ppad;
   a.tmem_cols = pl.tmem_cols;
   a.Xt = Xt;
@@ -578,9 +679,11 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.part = part;
   a.status = status;
   if (pl.form == kFormFP8 && (!uscale || !colinv)) return cudaErrorInvalidValue;
-  void (*kern)(const TcArgs) = pl.form == kFormBF16x3 ? fitness_tc_kernel<kFormBF16x3>
-                               : pl.form == kFormFP8  ? fitness_tc_kernel<kFormFP8>
-                                                      : fitness_tc_kernel<kFormBF16>;
+  if (pl.BN == 192 && pl.form != kFormBF16) return cudaErrorInvalidValue;
+  void (*kern)(const TcArgs) = pl.form == kFormBF16x3 ? fitness_tc_kernel<kFormBF16x3, false>
+                               : pl.form == kFormFP8  ? fitness_tc_kernel<kFormFP8, false>
+                               : pl.BN == 192         ? fitness_tc_kernel<kFormBF16, true>
+                                                      : fitness_tc_kernel<kFormBF16, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        pl.smem_bytes);
   if (e != cudaSuccess) return e;

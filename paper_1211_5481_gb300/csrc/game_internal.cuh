@@ -1,7 +1,7 @@
 // game_internal.cuh -- shared definitions of the CUDA path of libgame.so.
 //
 // Device data layout (all owned by the handle):
-//   Xt   [Mpad/128][N][128] FP32  features, tiled by blocks of 128 patterns and
+//   Xt   [Mpad/128][N][128] FP32  features (Mpad a multiple of 768), tiled by blocks of 128 patterns and
 //                                 feature-major inside a block, so one block is a
 //                                 contiguous, 16-byte-aligned run for bulk copies
 //                                 and a warp reading one feature of 32 patterns

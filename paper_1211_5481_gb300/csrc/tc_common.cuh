@@ -45,9 +45,11 @@ static __device__ void wait_bar_drain(uint32_t bar, uint32_t parity, int* status
   }
 }
 
-// sse += ((y - bias) - u * acc)^2 over 32 columns, two columns per packed op
-// (u = 1 except for FP8, where -u * acc + (y - bias) is one rounding as
-// (y - bias) - acc is for u = 1).
+// sse += ((y - bias) - u * acc)^2 over 32 columns, two columns per packed op.
+// SCALED = false: u = 1 and the residual is one packed subtraction; true
+// (FP8): -u * acc + (y - bias) as one packed FMA (one rounding, as the
+// subtraction is for u = 1).
+template <bool SCALED>
 __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* yc,
                                           uint64_t bias2, uint64_t negu2, uint64_t& s2) {
 #pragma unroll
@@ -55,10 +57,10 @@ __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* 
     const float4 yv = __ldg(reinterpret_cast<const float4*>(yc) + e4);
     const uint64_t ya = ptx::f2_sub(ptx::f2_pack(yv.x, yv.y), bias2);
     const uint64_t yb = ptx::f2_sub(ptx::f2_pack(yv.z, yv.w), bias2);
-    const uint64_t ra = ptx::f2_fma(negu2, ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]),
-                                                        __uint_as_float(v[4 * e4 + 1])), ya);
-    const uint64_t rb = ptx::f2_fma(negu2, ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]),
-                                                        __uint_as_float(v[4 * e4 + 3])), yb);
+    const uint64_t da = ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]), __uint_as_float(v[4 * e4 + 1]));
+    const uint64_t db = ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]), __uint_as_float(v[4 * e4 + 3]));
+    const uint64_t ra = SCALED ? ptx::f2_fma(negu2, da, ya) : ptx::f2_sub(ya, da);
+    const uint64_t rb = SCALED ? ptx::f2_fma(negu2, db, yb) : ptx::f2_sub(yb, db);
     s2 = ptx::f2_fma(ra, ra, s2);
     s2 = ptx::f2_fma(rb, rb, s2);
   }

@@ -30,6 +30,7 @@ CASES = [
     (4099, 40, 8, CHEB, 1),      # a single chromosome, K' = 320
     (513, 64, 10, TRIG, 33),     # K' = 1280, the longest batched contraction
     (6000, 32, 8, CHEB, 256),    # the large classification shape, reduced M
+    (3001, 48, 6, CHEB, 300),    # the surrogate workload's shape: 192-pattern tiles
 ]
 
 

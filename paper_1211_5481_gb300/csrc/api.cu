@@ -324,7 +324,10 @@ int ensure_surrogate(game_ctx* h, int rows) {
     s.K = h->s.K;
     if (dev_alloc(&s.w, n) != cudaSuccess || dev_alloc(&s.g, n) != cudaSuccess ||
         dev_alloc(&s.m, n) != cudaSuccess || dev_alloc(&s.v, n) != cudaSuccess ||
-        dev_alloc(&s.loss, 1) != cudaSuccess || dev_alloc(&s.tstat, 2) != cudaSuccess) {
+        dev_alloc(&s.loss, 1) != cudaSuccess || dev_alloc(&s.tstat, 2) != cudaSuccess ||
+        dev_alloc(&s.split_ws, (size_t)kMaxSplits * kSurrogateHidden *
+                                   (h->s.K > kSurrogateHidden ? h->s.K : kSurrogateHidden)) !=
+            cudaSuccess) {
       cudaGetLastError();
       return fail(GAME_ENOMEM, "surrogate parameters");
     }
@@ -519,7 +522,8 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->ufit);
   SurrogateDev& s = h->sd;
   float* sb[] = {s.w, s.g, s.m, s.v, s.Z1, s.H1, s.Z2, s.H2, s.dZ1, s.dZ2, s.out, s.dout,
-                 s.lterm, s.loss, h->off, h->pred, h->rX[0], h->rX[1], h->uX, h->upred};
+                 s.lterm, s.loss, s.split_ws, h->off, h->pred, h->rX[0], h->rX[1], h->uX,
+                 h->upred};
   for (float* b : sb) dev_free(b);
   dev_free(h->oplan);
   dev_free(h->flag);

@@ -322,6 +322,14 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
             }
           }
         }
+        // the next tile's feature blocks into L2, so its copy (issued once the
+        // expansion has released this one) reads L2 instead of HBM
+        if (it + 1 < my_tiles) {
+          const int64_t m1 = (t + G) * BN;
+          const int64_t b0 = m1 / kPatBlock, b1 = (m1 + BN - 1) / kPatBlock;
+          ptx::bulk_prefetch_l2(a.Xt + b0 * N * kPatBlock,
+                                (uint32_t)((b1 - b0 + 1) * N * kPatBlock * 4));
+        }
         ++issued;
       }
       if (issued > 0) wait_bar_drain(ptx::smem_addr(x_full), (issued - 1) & 1, a.status);

@@ -124,6 +124,7 @@ cudaError_t launch_rescore(const RescorePlan& pl, const Shape& s, const float* X
 constexpr int kSurrogateHidden = 256;
 constexpr float kAdamLr = 1e-3f, kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
 constexpr int kScreenMax = 16384;   // children screened per generation at most
+constexpr int kMaxSplits = 32;      // split-K of the surrogate's weight gradients
 struct SurrogateDev {
   int K, Bmax;
   int64_t step;            // Adam steps taken
@@ -135,6 +136,7 @@ struct SurrogateDev {
   float *out, *dout, *lterm;              // [Bmax]
   float* loss;             // [1]
   double* tstat;           // [2] mean and sd of the batch's log-fitness
+  float* split_ws;         // [kMaxSplits][256][max(K, 256)] split-K partial products
 };
 int64_t surrogate_param_count(int K);
 cudaError_t surrogate_init(const SurrogateDev& s, uint64_t seed, cudaStream_t st);

@@ -57,68 +57,95 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // C[m][n] = sum_k A(m, k) B(k, n), A(m, k) = A[m * am + k * ak], B(k, n) =
-// B[k * bk + n * bn]; FP32 accumulation in k order per thread. Epilogue
-// modes: 0 store C; 1 store Z = C + bias[n] to C and g(Z) (BF16-rounded when
-// round_out) to out2; 2 store C + bias[n].
-constexpr int kTM = 64, kTN = 64, kTK = 16;
+// B[k * bk + n * bn]; FP32 accumulation in k order per thread. 128 x 128
+// tiles, 256 threads, 8 x 8 outputs per thread, k-chunks of 16 through shared
+// memory; each operand tile is loaded with consecutive threads along its
+// contiguous dimension (ak == 1 or am == 1, bk == 1 or bn == 1). Split-K:
+// blockIdx.z takes k-range [z * kz, (z + 1) * kz) and, with splits > 1, writes
+// its partial product to C + z * M * ldc (reduced in order by splitk_reduce).
+// Epilogue modes (splits == 1): 0 store C; 1 store Z = C + bias[n] to C and
+// g(Z) (BF16-rounded when round_out) to out2; 2 store C + bias[n].
+constexpr int kTM = 128, kTN = 128, kTK = 16;
 __global__ void __launch_bounds__(256)
 gemm_kernel(int M, int N, int Kd, const float* __restrict__ A, int64_t am, int64_t ak,
             const float* __restrict__ B, int64_t bk, int64_t bn, int round_a, int round_b,
             float* __restrict__ C, int64_t ldc, int mode, const float* __restrict__ bias,
-            float* __restrict__ out2, int round_out) {
+            float* __restrict__ out2, int round_out, int kz) {
   __shared__ float As[kTK][kTM + 4];
   __shared__ float Bs[kTK][kTN + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-  float acc[4][4];
+  const int kbeg = blockIdx.z * kz;
+  const int kend = min(Kd, kbeg + kz);
+  float acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < Kd; k0 += kTK) {
-    for (int e = threadIdx.x; e < kTK * kTM; e += 256) {
-      const int kk = e / kTM, mm = e % kTM;
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const bool a_kc = ak == 1, b_kc = bk == 1;
+  for (int k0 = kbeg; k0 < kend; k0 += kTK) {
+#pragma unroll
+    for (int r = 0; r < (kTK * kTM) / 256; ++r) {
+      const int e = r * 256 + threadIdx.x;
+      const int kk = a_kc ? e % kTK : e / kTM;
+      const int mm = a_kc ? e / kTK : e % kTM;
       const int m = m0 + mm, k = k0 + kk;
-      float v = (m < M && k < Kd) ? A[(int64_t)m * am + (int64_t)k * ak] : 0.f;
+      const float v = (m < M && k < kend) ? A[(int64_t)m * am + (int64_t)k * ak] : 0.f;
       As[kk][mm] = round_a ? round_bf16(v) : v;
     }
-    for (int e = threadIdx.x; e < kTK * kTN; e += 256) {
-      const int kk = e / kTN, nn = e % kTN;
+#pragma unroll
+    for (int r = 0; r < (kTK * kTN) / 256; ++r) {
+      const int e = r * 256 + threadIdx.x;
+      const int kk = b_kc ? e % kTK : e / kTN;
+      const int nn = b_kc ? e / kTK : e % kTN;
       const int n = n0 + nn, k = k0 + kk;
-      float v = (n < N && k < Kd) ? B[(int64_t)k * bk + (int64_t)n * bn] : 0.f;
+      const float v = (n < N && k < kend) ? B[(int64_t)k * bk + (int64_t)n * bn] : 0.f;
       Bs[kk][nn] = round_b ? round_bf16(v) : v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kTK; ++kk) {
-      float a[4], b[4];
+      const float4 a_lo = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a_hi = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 b_lo = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 b_hi = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+      const float bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     __syncthreads();
   }
+  float* Cz = C + (int64_t)blockIdx.z * M * ldc;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty + 16 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 60 + ty * 4 + i);
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx + 16 * j;
+    for (int j = 0; j < 8; ++j) {
+      const int n = n0 + (j < 4 ? tx * 4 + j : 60 + tx * 4 + j);
       if (n >= N) continue;
       float v = acc[i][j];
       if (mode >= 1) v += bias[n];
-      C[(int64_t)m * ldc + n] = v;
+      Cz[(int64_t)m * ldc + n] = v;
       if (mode == 1) {
         const float gv = gelu(v);
         out2[(int64_t)m * ldc + n] = round_out ? round_bf16(gv) : gv;
       }
     }
+  }
+}
+
+// C[m][n] = sum over the splits, in order, of the partial products.
+__global__ void splitk_reduce_kernel(int64_t MN, int splits, const float* __restrict__ parts,
+                                     float* __restrict__ C) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += parts[z * MN + e];
+    C[e] = s;
   }
 }
 
@@ -429,6 +456,13 @@ __global__ void trust_kernel(int n, const float* __restrict__ pred, const int* _
   }
 }
 
+// Split-K factor of the weight-gradient GEMMs (reduction over the batch):
+// about 64 rows per split, at most kMaxSplits.
+int kGradSplits(int B) {
+  int sp = (B + 63) / 64;
+  return sp < 1 ? 1 : (sp > kMaxSplits ? kMaxSplits : sp);
+}
+
 int grid1d(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -438,10 +472,23 @@ int grid1d(int64_t n) {
 
 cudaError_t gemm(int M, int N, int Kd, const float* A, int64_t am, int64_t ak, const float* B,
                  int64_t bk, int64_t bn, int ra, int rb, float* C, int64_t ldc, int mode,
-                 const float* bias, float* out2, int round_out, cudaStream_t st) {
-  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM);
+                 const float* bias, float* out2, int round_out, cudaStream_t st,
+                 float* split_ws = nullptr, int splits = 1) {
+  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, splits);
+  int kz = (Kd + splits - 1) / splits;
+  kz = (kz + kTK - 1) / kTK * kTK;
+  if (splits > 1) {
+    // partial products into the workspace, then their sum in split order
+    gemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, split_ws, N, 0,
+                                      nullptr, nullptr, 0, kz);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    splitk_reduce_kernel<<<grid1d((int64_t)M * N), 256, 0, st>>>((int64_t)M * N, splits,
+                                                                  split_ws, C);
+    return cudaGetLastError();
+  }
   gemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, C, ldc, mode, bias,
-                                    out2, round_out);
+                                    out2, round_out, kz);
   return cudaGetLastError();
 }
 
@@ -508,7 +555,9 @@ cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const doub
   // dZ2 = dout w3 g'(Z2)
   dz2_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>(B, s.dout, w3, s.Z2, s.dZ2);
   // gW2 = dZ2^T H1, gb2 = colsum(dZ2)
-  e = gemm(kH, kH, B, s.dZ2, 1, kH, s.H1, kH, 1, 0, 0, gW2, kH, 0, nullptr, nullptr, 0, st);
+  const int splits = kGradSplits(B);
+  e = gemm(kH, kH, B, s.dZ2, 1, kH, s.H1, kH, 1, 0, 0, gW2, kH, 0, nullptr, nullptr, 0, st,
+           s.split_ws, splits);
   if (e != cudaSuccess) return e;
   colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ2, nullptr, gb2);
   // dZ1 = (dZ2 bf(W2)) g'(Z1)
@@ -516,7 +565,8 @@ cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const doub
   if (e != cudaSuccess) return e;
   gelu_bwd_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>((int64_t)B * kH, s.Z1, s.dZ1);
   // gW1 = dZ1^T bf(X), gb1 = colsum(dZ1)
-  e = gemm(kH, K, B, s.dZ1, 1, kH, X, K, 1, 0, 1, gW1, K, 0, nullptr, nullptr, 0, st);
+  e = gemm(kH, K, B, s.dZ1, 1, kH, X, K, 1, 0, 1, gW1, K, 0, nullptr, nullptr, 0, st,
+           s.split_ws, splits);
   if (e != cudaSuccess) return e;
   colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ1, nullptr, gb1);
   return cudaGetLastError();

@@ -64,7 +64,7 @@ def parse():
 # DRAM bytes per launch of the dominant kernel, read + write, from the ncu
 # capture summarised in profiles/fitness_tc_M1000000_N32_cheb8_P1024_ncu.md
 # (valid for that kernel version and workload only; None elsewhere)
-NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.77e6 + 2.96e6}
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.64e6 + 3.46e6}
 
 
 def load_peaks():

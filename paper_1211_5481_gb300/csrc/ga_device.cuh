@@ -14,11 +14,21 @@ namespace ga {
 constexpr int kPlanThreads = 1024;
 constexpr int kMaxElites = 256;
 
-__device__ __forceinline__ double rank_key(double f) { return isnan(f) ? CUDART_INF : f; }
+// Ranking key of a fitness value as an unsigned integer whose order is the
+// order of the values (NaN as +infinity, -0 as +0, so equal values tie as in
+// FP64 comparison): the GPU ranks with integer compares instead of the slow
+// FP64 pipe.
+__device__ __forceinline__ uint64_t rank_key(double f) {
+  if (isnan(f)) f = CUDART_INF;
+  if (f == 0.0) f = 0.0;
+  const uint64_t u = (uint64_t)__double_as_longlong(f);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+constexpr uint64_t kKeyMax = ~0ull;   // above every rank_key
 
-// (fa, a) ranks before (fb, b)
-__device__ __forceinline__ bool ranks_before(double fa, int a, double fb, int b) {
-  return fa < fb || (fa == fb && a < b);
+// (ka, a) ranks before (kb, b)
+__device__ __forceinline__ bool ranks_before(uint64_t ka, int a, uint64_t kb, int b) {
+  return ka < kb || (ka == kb && a < b);
 }
 
 // Gene e = p K + k of the initial population (uniform in [-1, 1)).
@@ -33,18 +43,18 @@ __device__ __forceinline__ float init_gene(uint64_t seed, int K, int64_t e) {
 __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restrict__ fit,
                                           uint64_t seed, uint32_t g, int4* __restrict__ plan) {
   __shared__ int elite[kMaxElites];
-  __shared__ double wkey[kPlanThreads / 32];
+  __shared__ uint64_t wkey[kPlanThreads / 32];
   __shared__ int widx[kPlanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // 1. elites, one block-wide arg-min per elite
   for (int e = 0; e < ga.E; ++e) {
-    double bk = CUDART_INF;
+    uint64_t bk = kKeyMax;
     int bi = 0x7fffffff;
     for (int p = tid; p < ga.P; p += kPlanThreads) {
       bool taken = false;
       for (int j = 0; j < e; ++j) taken |= (elite[j] == p);
       if (taken) continue;
-      const double k = rank_key(fit[p]);
+      const uint64_t k = rank_key(fit[p]);
       if (ranks_before(k, p, bk, bi)) {
         bk = k;
         bi = p;
@@ -52,7 +62,7 @@ __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restr
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      const uint64_t ok = __shfl_xor_sync(0xffffffffu, bk, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ranks_before(ok, oi, bk, bi)) {
         bk = ok;
@@ -69,7 +79,7 @@ __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restr
       bi = widx[lane];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        const uint64_t ok = __shfl_xor_sync(0xffffffffu, bk, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ranks_before(ok, oi, bk, bi)) {
           bk = ok;
@@ -89,14 +99,14 @@ __device__ __forceinline__ void plan_body(const GaDev& ga, const double* __restr
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       int win = -1;
-      double wk = 0.0;
+      uint64_t wk = 0;
       uint4 w = make_uint4(0, 0, 0, 0);
       for (int s = 0; s < ga.T; ++s) {
         if ((s & 3) == 0) w = philox4x32_10(seed, g, (uint32_t)q, (uint32_t)r,
                                             kTagTour | ((uint32_t)(s >> 2) << 8));
         const uint32_t word = (s & 3) == 0 ? w.x : (s & 3) == 1 ? w.y : (s & 3) == 2 ? w.z : w.w;
         const int c = (int)(((uint64_t)word * (uint64_t)ga.P) >> 32);
-        const double ck = rank_key(fit[c]);
+        const uint64_t ck = rank_key(fit[c]);
         if (win < 0 || ranks_before(ck, c, wk, win)) {
           win = c;
           wk = ck;

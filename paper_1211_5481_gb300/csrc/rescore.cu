@@ -33,15 +33,25 @@ constexpr int kSelThreads = 256;
 constexpr int kGroup = 8;       // candidates per evaluation group
 constexpr int kEvalThreads = 256;
 
-__device__ __forceinline__ bool key_before(double fa, int a, double fb, int b) {
+// Fitness as an order-preserving unsigned key (NaN as +infinity, -0 as +0),
+// so the ranking runs on integer compares instead of the slow FP64 pipe.
+__device__ __forceinline__ uint64_t fit_key(double f) {
+  if (isnan(f)) f = CUDART_INF;
+  if (f == 0.0) f = 0.0;
+  const uint64_t u = (uint64_t)__double_as_longlong(f);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+constexpr uint64_t kNoKey = ~0ull;
+
+__device__ __forceinline__ bool key_before(uint64_t fa, int a, uint64_t fb, int b) {
   return fa < fb || (fa == fb && a < b);
 }
 
 // Warp-wide arg-min of (key, index); every lane receives the winner.
-__device__ __forceinline__ void warp_argmin(double& k, int& i) {
+__device__ __forceinline__ void warp_argmin(uint64_t& k, int& i) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ok = __shfl_xor_sync(0xffffffffu, k, o);
+    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k, o);
     const int oi = __shfl_xor_sync(0xffffffffu, i, o);
     if (key_before(ok, oi, k, i)) {
       k = ok;
@@ -52,23 +62,23 @@ __device__ __forceinline__ void warp_argmin(double& k, int& i) {
 
 // Sorted list of kMaxRescore (key, index) pairs held in registers.
 struct TopList {
-  double k[kMaxRescore];
+  uint64_t k[kMaxRescore];
   int i[kMaxRescore];
   __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int j = 0; j < kMaxRescore; ++j) {
-      k[j] = CUDART_INF;
+      k[j] = kNoKey;
       i[j] = 0x7fffffff;
     }
   }
-  __device__ __forceinline__ void insert(double key, int idx) {
+  __device__ __forceinline__ void insert(uint64_t key, int idx) {
     if (!key_before(key, idx, k[kMaxRescore - 1], i[kMaxRescore - 1])) return;
     k[kMaxRescore - 1] = key;
     i[kMaxRescore - 1] = idx;
 #pragma unroll
     for (int j = kMaxRescore - 1; j > 0; --j) {
       if (key_before(k[j], i[j], k[j - 1], i[j - 1])) {
-        const double tk = k[j];
+        const uint64_t tk = k[j];
         const int ti = i[j];
         k[j] = k[j - 1];
         i[j] = i[j - 1];
@@ -83,25 +93,22 @@ struct TopList {
       k[j] = k[j + 1];
       i[j] = i[j + 1];
     }
-    k[kMaxRescore - 1] = CUDART_INF;
+    k[kMaxRescore - 1] = kNoKey;
     i[kMaxRescore - 1] = 0x7fffffff;
   }
 };
 
 __global__ void __launch_bounds__(kSelThreads)
 select_top_kernel(const double* __restrict__ fit, int P, int n, int* __restrict__ cand) {
-  __shared__ double wk[kSelThreads / 32][kMaxRescore];
+  __shared__ uint64_t wk[kSelThreads / 32][kMaxRescore];
   __shared__ int wi[kSelThreads / 32][kMaxRescore];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   TopList L;
   L.clear();
-  for (int p = tid; p < P; p += kSelThreads) {
-    const double f = fit[p];
-    L.insert(isnan(f) ? CUDART_INF : f, p);
-  }
+  for (int p = tid; p < P; p += kSelThreads) L.insert(fit_key(fit[p]), p);
   // each warp: n rounds of arg-min over its lanes' list heads
   for (int r = 0; r < n; ++r) {
-    double k = L.k[0];
+    uint64_t k = L.k[0];
     int i = L.i[0];
     warp_argmin(k, i);
     if (L.i[0] == i && i != 0x7fffffff) L.pop_front();
@@ -120,7 +127,7 @@ select_top_kernel(const double* __restrict__ fit, int P, int n, int* __restrict_
       L.i[j] = wi[lane][j];
     }
   for (int r = 0; r < n; ++r) {
-    double k = L.k[0];
+    uint64_t k = L.k[0];
     int i = L.i[0];
     warp_argmin(k, i);
     if (L.i[0] == i && i != 0x7fffffff) L.pop_front();

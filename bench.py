@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--M", type=int, default=1_000_000, help="patterns (smaller for profiling)")
-    ap.add_argument("--form", choices=["bf16", "bf16x3", "fp8", "fp32"], default="bf16")
+    ap.add_argument("--form", choices=["bf16", "bf16x3", "fp8", "fp32", "gram"], default="bf16")
     ap.add_argument("--workload", choices=["classification", "batched", "surrogate"],
                     default="classification",
                     help="batched: 256 independent runs of uneven shape, one graph per "
@@ -429,9 +429,12 @@ def main():
     yd = torch.from_numpy(pr.y).to(dev)
     game.load()
     prec = {"fp32": game.GAME_PREC_FP32, "bf16": game.GAME_PREC_BF16,
-            "bf16x3": game.GAME_PREC_BF16X3, "fp8": game.GAME_PREC_FP8}[args.form]
-    tensor = prec != game.GAME_PREC_FP32
+            "bf16x3": game.GAME_PREC_BF16X3, "fp8": game.GAME_PREC_FP8,
+            "gram": game.GAME_PREC_GRAM}[args.form]
+    tensor = prec not in (game.GAME_PREC_FP32, game.GAME_PREC_GRAM)
+    t_create = time.perf_counter()
     g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2)
+    t_create = time.perf_counter() - t_create
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def timed_steps(handle, steps, warmup):
@@ -489,6 +492,15 @@ def main():
                     "bf16_tflops_sustained", peaks["bf16_tflops"])) * ratio),
                 "mma_tflops": achieved_tflops * mma_per_product,
                 "kernel": "fitness_tc_kernel", "kernel_ms": fit_ms}
+    elif prec == game.GAME_PREC_GRAM:
+        # FP64 quadratic forms: 2 P K^2 + 2 P K flop per generation
+        gflops = (2.0 * P * K * K + 2.0 * P * K) / (fit_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": gflops, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": gflops / 1.25, "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate (not in the measured peaks)",
+                "kernel": "quad_kernel", "kernel_ms": fit_ms,
+                "gram_build_s": t_create,
+                "note": "evaluations implicit: fit = (y.y - 2 a.b + a^T G a) / M"}
     else:
         props = torch.cuda.get_device_properties(dev)
         peak = props.multi_processor_count * 128 * 2 * float(peaks["sm_max_mhz"]) * 1e6 / 1e12
@@ -556,7 +568,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3",
-                                               "fp8": "e4m3"}[args.form],
+                                               "fp8": "e4m3", "gram": "f64"}[args.form],
         "data": "synthetic",
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "basis": "chebyshev", "contraction": args.form,

@@ -62,6 +62,14 @@ extern "C" {
                               from the training set), genes by the inverse
                               and a per-chromosome factor restored in the
                               epilogue */
+#define GAME_PREC_GRAM 4   /* Gram form of the MSE in FP64: with
+                              phi~ = (1, phi_1, ..., phi_{K-1}),
+                              fit = (y.y - 2 a.b + a^T G a) / M where
+                              G = sum phi~ phi~^T and b = sum y phi~ are built
+                              once per handle (FP64 expansion and sums); a
+                              generation then costs P K^2 FP64 multiply-adds
+                              instead of M P K; exact to FP64 rounding (no
+                              re-scoring) */
 
 typedef struct game_ctx* game_t;
 
@@ -308,6 +316,10 @@ int game_batch_fitness_ms(game_batch_t b, int32_t reps, double* ms_out);
 int game_batch_sync(game_batch_t b);
 /* Releases the batch (NULL is accepted). */
 int game_batch_destroy(game_batch_t b);
+
+/* The Gram form's G [K][K], b [K] and y.y (FP64; built on first use; any
+ * output may be NULL; host or device). Synchronises. */
+int game_gram(game_t h, double* G_out, double* b_out, double* yy_out);
 
 /* Waits for the handle's stream and reports a kernel timeout, if any. */
 int game_sync(game_t h);

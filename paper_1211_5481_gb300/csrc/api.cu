@@ -93,6 +93,10 @@ struct game_ctx {
   float* a0 = nullptr;
   float* uscale = nullptr;     // FP8: per-chromosome scales [cap_P]
   double* part = nullptr;
+  // Gram form of the MSE (built once, at the first GAME_PREC_GRAM use)
+  double* G = nullptr;
+  double* gb = nullptr;
+  double* gyy = nullptr;
   // FP8 column scales of the expansion (computed once, at the first FP8 use)
   unsigned int* colmax = nullptr;
   float* colscale = nullptr;
@@ -179,7 +183,36 @@ void stage_end(game_ctx* h, cudaEvent_t start, int kind) {
 
 bool valid_precision(int prec) {
   return prec == GAME_PREC_FP32 || prec == GAME_PREC_BF16 || prec == GAME_PREC_BF16X3 ||
-         prec == GAME_PREC_FP8;
+         prec == GAME_PREC_FP8 || prec == GAME_PREC_GRAM;
+}
+
+// G, b, yy of the training set (FP64), once per handle; the build's scratch
+// (a chunk of the FP64 design matrix and split partial sums) is released.
+int ensure_gram(game_ctx* h) {
+  if (h->G) return GAME_OK;
+  const int K = h->s.K;
+  const int64_t rows = gram_chunk_rows(h->s);
+  double* phi = nullptr;
+  double* part = nullptr;
+  if (dev_alloc(&h->G, (size_t)K * K) != cudaSuccess || dev_alloc(&h->gb, (size_t)K) != cudaSuccess ||
+      dev_alloc(&h->gyy, 1) != cudaSuccess || dev_alloc(&phi, (size_t)rows * K) != cudaSuccess ||
+      dev_alloc(&part, (size_t)kGramSplits * K * K) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(phi);
+    dev_free(part);
+    dev_free(h->G);
+    dev_free(h->gb);
+    dev_free(h->gyy);
+    h->G = nullptr;
+    h->gb = h->gyy = nullptr;
+    return fail(GAME_ENOMEM, "Gram matrix");
+  }
+  cudaError_t e = launch_gram_build(h->s, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  dev_free(phi);
+  dev_free(part);
+  if (e != cudaSuccess) return cuda_fail(e, "Gram build");
+  return GAME_OK;
 }
 
 // tensor-core operand form of a reduced-precision GAME_PREC_*
@@ -209,6 +242,7 @@ int ensure_colscales(game_ctx* h) {
 }
 
 int ensure_scratch(game_ctx* h, int P, int prec) {
+  if (prec == GAME_PREC_GRAM) return ensure_gram(h);
   const int Ppad = ceil_div(P, 128) * 128;
   if (Ppad > h->cap_P) {
     dev_free(h->a0);
@@ -267,7 +301,11 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
   if (rc) return rc;
   const int Ppad = ceil_div(P, 128) * 128;
   cudaEvent_t t0;
-  if (prec == GAME_PREC_FP32) {
+  if (prec == GAME_PREC_GRAM) {
+    t0 = stage_begin(h);
+    CK(launch_gram_fitness(h->s, dpop, P, h->G, h->gb, h->gyy, dfit, h->st));
+    stage_end(h, t0, kFitness);
+  } else if (prec == GAME_PREC_FP32) {
     const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
     t0 = stage_begin(h);
     CK(launch_pack_fp32(dpop, P, Ppad, h->s, pl.Kc, h->popT, h->a0, h->st));
@@ -311,7 +349,7 @@ int eval_state(game_ctx* h) {
   int rc = eval_device(h, h->pop[h->cur], h->prm.P, h->prm.precision, h->fit);
   if (rc) return rc;
   const int n = h->prm.rescore_top < h->prm.P ? h->prm.rescore_top : h->prm.P;
-  if (h->prm.precision != GAME_PREC_FP32 && n > 0)
+  if (h->prm.precision != GAME_PREC_FP32 && h->prm.precision != GAME_PREC_GRAM && n > 0)
     return rescore_device(h, h->pop[h->cur], h->prm.P, n, h->fit);
   return GAME_OK;
 }
@@ -514,6 +552,9 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->popA);
   dev_free(h->a0);
   dev_free(h->uscale);
+  dev_free(h->G);
+  dev_free(h->gb);
+  dev_free(h->gyy);
   dev_free(h->colmax);
   dev_free(h->colscale);
   dev_free(h->colinv);
@@ -1020,6 +1061,18 @@ int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n
   if (keep_out)
     CK(cudaMemcpyAsync(keep_out, h->flag, (size_t)h->last_n * sizeof(int32_t), cudaMemcpyDefault,
                        h->st));
+  return check_status(h);
+}
+
+int game_gram(game_t h, double* G_out, double* b_out, double* yy_out) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  int rc = ensure_gram(h);
+  if (rc) return rc;
+  const int K = h->s.K;
+  if (G_out) CK(cudaMemcpyAsync(G_out, h->G, (size_t)K * K * sizeof(double), cudaMemcpyDefault, h->st));
+  if (b_out) CK(cudaMemcpyAsync(b_out, h->gb, (size_t)K * sizeof(double), cudaMemcpyDefault, h->st));
+  if (yy_out) CK(cudaMemcpyAsync(yy_out, h->gyy, sizeof(double), cudaMemcpyDefault, h->st));
   return check_status(h);
 }
 

@@ -158,6 +158,18 @@ cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred,
 cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int* pos,
                             const double* fit_kept, float* r_out, int* trusted, cudaStream_t st);
 
+// gram.cu -- the Gram form of the MSE (FP64)
+constexpr int kGramSplits = 8;   // row splits of a chunk's G accumulation
+int64_t gram_chunk_rows(const Shape& s);
+// G [K][K], b [K], yy [1] of the training set; phi_chunk [gram_chunk_rows][K]
+// and part [kGramSplits][K][K] are scratch.
+cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, double* G,
+                              double* b, double* yy, double* phi_chunk, double* part,
+                              cudaStream_t st);
+cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const double* G,
+                                const double* b, const double* yy, double* fit,
+                                cudaStream_t st);
+
 // api.cu
 void record_error(const char* msg);
 // reduce.cu

@@ -1,0 +1,276 @@
+// gram.cu -- the Gram form of the MSE fitness (FP64).
+//
+// With phi~(x) = (1, phi_1(x), ..., phi_{K-1}(x)) the expansion of Eq. 1 /
+// Eq. 6 with a leading 1 for the bias gene, the output of Eq. 2 is
+// Out_p(m) = a_p . phi~(x_m), so the MSE of Eq. 3 is a quadratic form:
+//   fit_p = (yy - 2 a_p . b + a_p^T G a_p) / M,
+//   G = sum_m phi~(x_m) phi~(x_m)^T [K][K], b = sum_m y_m phi~(x_m), yy = sum_m y_m^2.
+// G, b and yy depend only on the training set: they are accumulated once per
+// handle (FP64 expansion -- the Chebyshev recurrence, or sin / cos of x and
+// the angle recurrence -- and FP64 sums), after which a generation costs
+// P K^2 FP64 multiply-adds instead of M P K. The subtraction cancels when the
+// fit is good (fit << yy / M), which is why everything here is FP64.
+//
+// Accumulation: the patterns are taken in chunks of up to kChunk; a chunk's
+// design matrix Phi [mc][K] (FP64) is written by expand_kernel, then
+// gram_accum_kernel adds Phi^T Phi into the upper triangle of G (64 x 64
+// tiles, each thread a 4 x 4 block, the chunk's rows in order) and
+// vec_accum_kernel adds Phi^T y and y^T y. Every sum runs in a fixed order
+// (chunks in sequence, rows in order within a chunk), so G is reproducible.
+// The quadratic forms: quad_kernel, one CTA per 8 chromosomes, thread t owns
+// rows t, t + 256, ... of G a_p and reads G column-wise (G is symmetric, so
+// G[k2][k1] over k2 is a coalesced column read), then a fixed-order CTA sum.
+#include <math_constants.h>
+
+#include "game_internal.cuh"
+
+namespace game {
+
+namespace {
+
+constexpr int kGT = 64;        // G tile
+constexpr int kQuadGroup = 8;  // chromosomes per quad CTA at most
+
+// Phi[r][k] for patterns m0 + r (r < mc), FP64; column 0 is 1.
+__global__ void expand_kernel(int64_t m0, int mc, int N, int d, int basis, int K,
+                              const float* __restrict__ Xt, double* __restrict__ Phi) {
+  const int B = basis == GAME_BASIS_TRIG ? 2 : 1;
+  const int64_t n = (int64_t)mc * N;   // one thread per (pattern, feature)
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / N), i = (int)(e % N);
+    const int64_t m = m0 + r;
+    const double x =
+        (double)Xt[(m / kPatBlock) * (int64_t)N * kPatBlock + (int64_t)i * kPatBlock + m % kPatBlock];
+    double* row = Phi + (int64_t)r * K;
+    if (i == 0) row[0] = 1.0;
+    const int64_t base = 1 + (int64_t)i * B * d;
+    if (basis == GAME_BASIS_CHEB) {
+      double tm = 1.0, t = x;
+      for (int j = 1; j <= d; ++j) {
+        row[base + j - 1] = t;
+        const double tn = 2.0 * x * t - tm;
+        tm = t;
+        t = tn;
+      }
+    } else {
+      double s1, c1;
+      sincos(x, &s1, &c1);
+      for (int bb = 0; bb < 2; ++bb) {
+        double fm = bb ? 0.0 : 1.0, f = bb ? s1 : c1;
+        for (int j = 1; j <= d; ++j) {
+          row[base + bb * d + j - 1] = f;
+          const double fn = 2.0 * c1 * f - fm;
+          fm = f;
+          f = fn;
+        }
+      }
+    }
+  }
+}
+
+// part[z][k1][k2] = sum over rows r of split z of Phi[r][k1] Phi[r][k2], for
+// the tile (blockIdx.y, blockIdx.x) of the upper triangle (tiles with
+// ti > tj skip); split z = blockIdx.z takes rows [z rs, (z + 1) rs).
+__global__ void __launch_bounds__(256)
+gram_accum_kernel(int mc, int rs, int K, const double* __restrict__ Phi,
+                  double* __restrict__ part) {
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (ti > tj) return;
+  const int rlo = blockIdx.z * rs, rhi = min(mc, rlo + rs);
+  __shared__ double Ps[16][2 * kGT];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int k10 = ti * kGT, k20 = tj * kGT;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int r0 = rlo; r0 < rhi; r0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 2 * kGT; e += 256) {
+      const int rr = e / (2 * kGT), c = e % (2 * kGT);
+      const int k = c < kGT ? k10 + c : k20 + (c - kGT);
+      Ps[rr][c] = (r0 + rr < rhi && k < K) ? Phi[(int64_t)(r0 + rr) * K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 16; ++rr) {
+      double a[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Ps[rr][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bv[v] = Ps[rr][kGT + tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double* Pz = part + (int64_t)blockIdx.z * K * K;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int k1 = k10 + ty + 16 * u, k2 = k20 + tx + 16 * v;
+      if (k1 < K && k2 < K && k1 <= k2) Pz[(int64_t)k1 * K + k2] = acc[u][v];
+    }
+}
+
+// G[k1][k2] += sum over the splits, in order, of part[z][k1][k2] (upper triangle).
+__global__ void gram_add_kernel(int K, int splits, const double* __restrict__ part,
+                                double* __restrict__ G) {
+  const int64_t n = (int64_t)K * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k1 = (int)(e / K), k2 = (int)(e % K);
+    if (k1 > k2) continue;
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[z * n + e];
+    G[e] += s;
+  }
+}
+
+// b[k] += sum_r Phi[r][k] y[m0 + r]; yy += sum_r y^2 (thread 0 of block 0)
+__global__ void vec_accum_kernel(int64_t m0, int mc, int K, const double* __restrict__ Phi,
+                                 const float* __restrict__ y, double* __restrict__ b,
+                                 double* __restrict__ yy) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < K) {
+    double s = 0.0;
+    for (int r = 0; r < mc; ++r) s = fma(Phi[(int64_t)r * K + k], (double)y[m0 + r], s);
+    b[k] += s;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int r = 0; r < mc; ++r) {
+      const double v = y[m0 + r];
+      s = fma(v, v, s);
+    }
+    *yy += s;
+  }
+}
+
+// Lower triangle from the upper one.
+__global__ void mirror_kernel(int K, double* __restrict__ G) {
+  const int64_t n = (int64_t)K * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k1 = (int)(e / K), k2 = (int)(e % K);
+    if (k1 > k2) G[e] = G[(int64_t)k2 * K + k1];
+  }
+}
+
+// fit_p = (yy - 2 a_p . b + a_p^T G a_p) / M for grp <= 8 chromosomes per CTA.
+__global__ void __launch_bounds__(256)
+quad_kernel(int P, int K, int64_t M, int grp, const float* __restrict__ pop,
+            const double* __restrict__ G, const double* __restrict__ b,
+            const double* __restrict__ yy, double* __restrict__ fit) {
+  extern __shared__ double as[];   // [8][K] genes of the group, FP64 (rows >= grp zero)
+  __shared__ double red[kQuadGroup][8];
+  const int p0 = blockIdx.x * grp;
+  const int ng = min(grp, P - p0);
+  for (int e = threadIdx.x; e < grp * K; e += 256) {
+    const int q = e / K, k = e % K;
+    as[e] = q < ng ? (double)pop[(int64_t)(p0 + q) * K + k] : 0.0;
+  }
+  __syncthreads();
+  double quad[kQuadGroup], lin[kQuadGroup];
+#pragma unroll
+  for (int q = 0; q < kQuadGroup; ++q) {
+    quad[q] = 0.0;
+    lin[q] = 0.0;
+  }
+  for (int k1 = threadIdx.x; k1 < K; k1 += 256) {
+    double ga[kQuadGroup];
+#pragma unroll
+    for (int q = 0; q < kQuadGroup; ++q) ga[q] = 0.0;
+    for (int k2 = 0; k2 < K; ++k2) {
+      const double g = G[(int64_t)k2 * K + k1];   // = G[k1][k2]
+#pragma unroll
+      for (int q = 0; q < kQuadGroup; ++q)
+        if (q < grp) ga[q] = fma(g, as[q * K + k2], ga[q]);
+    }
+    const double bk = b[k1];
+#pragma unroll
+    for (int q = 0; q < kQuadGroup; ++q)
+      if (q < grp) {
+        quad[q] = fma(as[q * K + k1], ga[q], quad[q]);
+        lin[q] = fma(as[q * K + k1], bk, lin[q]);
+      }
+  }
+  // fixed-order CTA sums: lanes by xor-butterfly, then the 8 warps in order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kQuadGroup; ++q) {
+    double v = quad[q] - 2.0 * lin[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < ng) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    fit[p0 + threadIdx.x] = (*yy + s) / (double)M;
+  }
+}
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 16384) b = 16384;
+  return (int)b;
+}
+
+}  // namespace
+
+int64_t gram_chunk_rows(const Shape& s) {
+  // Phi chunk of at most 64k patterns and at most 256 MB
+  int64_t rows = (int64_t)(256ll * 1024 * 1024) / ((int64_t)s.K * 8);
+  if (rows > 65536) rows = 65536;
+  if (rows < 16) rows = 16;
+  return rows;
+}
+
+cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, double* G,
+                              double* b, double* yy, double* phi_chunk, double* part,
+                              cudaStream_t st) {
+  const int K = s.K;
+  cudaError_t e = cudaMemsetAsync(G, 0, (size_t)K * K * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, (size_t)K * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(yy, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int64_t CH = gram_chunk_rows(s);
+  const int KT = (K + kGT - 1) / kGT;
+  for (int64_t m0 = 0; m0 < s.M; m0 += CH) {
+    const int mc = (int)(s.M - m0 < CH ? s.M - m0 : CH);
+    expand_kernel<<<blocks_for((int64_t)mc * s.N), 256, 0, st>>>(m0, mc, s.N, s.d, s.basis, K,
+                                                                Xt, phi_chunk);
+    const int rs = (mc + kGramSplits - 1) / kGramSplits;
+    gram_accum_kernel<<<dim3(KT, KT, kGramSplits), 256, 0, st>>>(mc, rs, K, phi_chunk, part);
+    gram_add_kernel<<<blocks_for((int64_t)K * K), 256, 0, st>>>(K, kGramSplits, part, G);
+    vec_accum_kernel<<<(K + 255) / 256, 256, 0, st>>>(m0, mc, K, phi_chunk, y, b, yy);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  mirror_kernel<<<blocks_for((int64_t)K * K), 256, 0, st>>>(K, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const double* G,
+                                const double* b, const double* yy, double* fit,
+                                cudaStream_t st) {
+  // as many chromosomes per CTA (<= 8) as fit in 200 KB of FP64 genes
+  int grp = (int)((200 * 1024) / ((size_t)s.K * sizeof(double)));
+  if (grp > kQuadGroup) grp = kQuadGroup;
+  if (grp < 1) grp = 1;
+  const size_t smem = (size_t)grp * s.K * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  quad_kernel<<<(P + grp - 1) / grp, 256, smem, st>>>(P, s.K, s.M, grp, pop, G, b, yy, fit);
+  return cudaGetLastError();
+}
+
+}  // namespace game

@@ -28,6 +28,7 @@ GAME_PREC_FP32 = 0
 GAME_PREC_BF16 = 1
 GAME_PREC_BF16X3 = 2
 GAME_PREC_FP8 = 3
+GAME_PREC_GRAM = 4
 
 _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
               GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}
@@ -41,7 +42,7 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_batch_get_tiles", "game_batch_fitness_ms", "game_batch_sync",
             "game_batch_destroy", "game_surrogate_predict", "game_surrogate_grad",
             "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
-            "game_surrogate_last")
+            "game_surrogate_last", "game_gram")
 
 
 class GameError(RuntimeError):
@@ -152,6 +153,7 @@ def load(build_if_missing: bool = True):
         "game_surrogate_params": [vp, vp, ctypes.POINTER(i64)],
         "game_surrogate_set_params": [vp, vp],
         "game_surrogate_last": [vp, vp, vp, ctypes.POINTER(i32), vp, vp],
+        "game_gram": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -309,6 +311,14 @@ class Game:
 
     def generation(self, seed):
         game_generation(self.h, seed)
+
+    def gram(self):
+        """(G [K][K], b [K], y.y) of the Gram form, FP64."""
+        G = np.zeros((self.K, self.K), dtype=np.float64)
+        b = np.zeros(self.K, dtype=np.float64)
+        yy = np.zeros(1, dtype=np.float64)
+        _check(load().game_gram(self.h, _ptr(G), _ptr(b), _ptr(yy)))
+        return G, b, float(yy[0])
 
     # ---- fitness surrogate (numpy in / out) ----
     def surrogate_predict(self, pop):

@@ -108,7 +108,7 @@ __global__ void breed_batch_kernel(const BatchGaRun* __restrict__ g,
 }
 
 // One warp per chromosome of all runs (chrom_begin: prefix sums of P_r):
-// fit_r[p] = sum over the run's tiles and halves, in order, / M_r. With
+// fit_r[p] = sum over the run's tiles, in order, / M_r. With
 // inc, the run's generation counter advances (the reduce is the last stage
 // of a generation).
 __global__ void reduce_batch_kernel(const BatchRun* __restrict__ runs,
@@ -130,7 +130,7 @@ __global__ void reduce_batch_kernel(const BatchRun* __restrict__ runs,
   const double* col = part + B.part_base + p;
   double s = 0.0;
   for (int t = lane; t < B.ntiles; t += 32)
-    s += col[(int64_t)(2 * t) * B.Ppad] + col[(int64_t)(2 * t + 1) * B.Ppad];
+    s += col[(int64_t)t * B.Ppad];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
@@ -272,7 +272,7 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
   for (int r : which) {
     BatchRun& R = runs[r];
     R.part_base = part_total;
-    part_total += (int64_t)2 * R.ntiles * R.Ppad;
+    part_total += (int64_t)R.ntiles * R.Ppad;
     KBmax = std::max(KBmax, R.KB);
     bn_max = std::max(bn_max, R.BN);
     phi_bytes = std::max(phi_bytes, R.KB * R.BN * 128);

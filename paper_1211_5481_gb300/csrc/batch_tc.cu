@@ -23,7 +23,7 @@
 // Roles as in fitness_tc.cu: warp 0 gene-block producer, warp 1 MMA issuer
 // and TMEM owner, warp 2 feature producer, warps 4-11 epilogue, warps 12-15
 // expansion. Each item writes its FP64 partial sums to its own rows,
-// part[part_base_r + (2 t + half) Ppad_r + p], so the result does not depend
+// part[part_base_r + t Ppad_r + p], so the result does not depend
 // on which CTA took the item; the batched reduce adds a problem's rows in
 // tile order. All waits are bounded (2 s) as in fitness_tc.cu.
 #include "basis.cuh"
@@ -40,10 +40,13 @@ using namespace tc;
 constexpr uint32_t kABytes = 128 * 128;
 constexpr int kWarps = 16;
 constexpr int kThreads = kWarps * 32;
+// Items carry 1-2 chromosome tiles, so the expansion, not the epilogue, is
+// the busy role: 4 epilogue warps (each thread one chromosome row, all of a
+// tile's columns) and 8 expansion warps.
 constexpr int kEpiWarp0 = 4;
-constexpr int kEpiThreads = 256;
-constexpr int kBasisWarp0 = 12;
-constexpr int kBasisThreads = 128;
+constexpr int kEpiThreads = 128;
+constexpr int kBasisWarp0 = 8;
+constexpr int kBasisThreads = 256;
 constexpr int kStages = 4;
 
 struct BSmem {
@@ -215,6 +218,15 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
             ptx::bulk_g2s(ptx::smem_addr(xs + i * BN), R.Xt + (blk * N + i) * kPatBlock + off,
                           (uint32_t)BN * 4, ptx::smem_addr(x_full));
         }
+        // the next item's feature blocks into L2, so its copy reads L2
+        if (it + 1 < it1) {
+          const int2 nx = a.items[a.sched[it + 1]];
+          const BatchRun R2 = a.runs[nx.x];
+          const int64_t m1 = (int64_t)nx.y * R2.BN;
+          const int64_t b0 = m1 / kPatBlock, b1 = (m1 + R2.BN - 1) / kPatBlock;
+          ptx::bulk_prefetch_l2(R2.Xt + b0 * R2.N * kPatBlock,
+                                (uint32_t)((b1 - b0 + 1) * R2.N * kPatBlock * 4));
+        }
         ++issued;
       }
       if (issued > 0) wait_bar_drain(ptx::smem_addr(x_full), (issued - 1) & 1, a.status);
@@ -222,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
   } else if (warp >= kEpiWarp0 && warp < kBasisWarp0) {
     // ---------------- epilogue ----------------
     const int qw = warp & 3;
-    const int half = (warp - kEpiWarp0) >> 2;
+
     const int row = qw * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(qw * 32) << 16;
     const uint64_t negu2 = ptx::f2_pack(-1.f, -1.f);
@@ -232,14 +244,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       const int2 item = a.items[a.sched[it]];
       const BatchRun R = a.runs[item.x];
       const int BN = R.BN;
-      const int NH = BN >= 64 ? 2 : 1;
-      const int HW = BN / NH;
-      const int col_lo = half * HW;
+      const int HW = BN;   // all of the tile's columns
+      const int col_lo = 0;
       const int64_t m0 = (int64_t)item.y * BN;
       const int64_t rem = R.M - m0 - col_lo;
-      const int valid = (half >= NH || rem <= 0) ? 0 : (rem >= HW ? HW : (int)rem);
+      const int valid = rem <= 0 ? 0 : (rem >= HW ? HW : (int)rem);
       const float* yt = R.y + m0 + col_lo;
-      double* prow = a.part + R.part_base + (int64_t)(2 * item.y + half) * R.Ppad;
+      double* prow = a.part + R.part_base + (int64_t)item.y * R.Ppad;
       for (int c = 0; c < R.C; ++c) {
         const uint32_t buf = acc_it & 1, u = acc_it >> 1;
         ok = wait_bar(ptx::smem_addr(&acc_full[buf]), u & 1, abort_flag, a.status);
@@ -317,13 +328,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       for (int cid = bt; cid < KB * 8; cid += kBasisThreads)
         tb[cid] = chunk_desc(cid, R.basis, R.d, R.Kp);
       ptx::named_bar(1, kBasisThreads);
-      const int XW = BN < 128 ? BN : 128;
-      const int Rr = BN / XW;
-      const int QS = 128 / XW;
-      const int r0 = bt % XW, q0 = bt / XW;
-      const int r1 = r0 + 128;
+      // one row per thread (256 threads, BN <= 256 rows), 256 / BN unit groups
+      const int XW = BN < 128 ? BN : 128;       // patterns per feature row in xs
+      const int RW = BN;
+      const int QS = kBasisThreads / RW;
+      const int r0 = bt % RW, q0 = bt / RW;
       const float* xrow0 = xs + (r0 >> 7) * N * XW + (r0 % XW);
-      const float* xrow1 = xs + (r1 >> 7) * N * XW + (r1 % XW);
       if (!dead) dead = !wait_bar(ptx::smem_addr(x_full), items_done & 1, abort_flag, a.status);
       if (BN != prev_bn)
         for (int kb = 0; kb < KBmax && !dead; ++kb)
@@ -337,16 +347,11 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
         uint8_t* phik = phi + (size_t)kb * BN * 128;
         for (int qd = q0; qd < 8; qd += QS) {
           const uint32_t desc = tb[kb * 8 + qd];
-          float va[8], vb[8];
+          float va[8];
           gen_chunk(desc, R.basis, R.d, N, xrow0, XW, va);
-          if (Rr == 2) gen_chunk(desc, R.basis, R.d, N, xrow1, XW, vb);
           *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
               make_uint4(bf16x2_bits(va[0], va[1]), bf16x2_bits(va[2], va[3]),
                          bf16x2_bits(va[4], va[5]), bf16x2_bits(va[6], va[7]));
-          if (Rr == 2)
-            *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
-                make_uint4(bf16x2_bits(vb[0], vb[1]), bf16x2_bits(vb[2], vb[3]),
-                           bf16x2_bits(vb[4], vb[5]), bf16x2_bits(vb[6], vb[7]));
         }
         ptx::fence_proxy_async_smem();
         ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));

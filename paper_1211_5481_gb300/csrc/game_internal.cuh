@@ -103,7 +103,7 @@ struct BatchArgs {
   const int2* items;        // (problem, pattern tile), problem-major
   const int* sched;         // item indices, grouped by CTA
   const int* cta_begin;     // [grid + 1] ranges of sched per CTA
-  double* part;             // partial rows: part_base_r + (2 t + half) Ppad_r
+  double* part;             // partial rows: part_base_r + t Ppad_r
   int* status;
   int KBmax, bn_max, phi_bytes, x_bytes, tmem_cols;
 };

@@ -9,7 +9,7 @@ data generated on the host and uploaded before timing. One step is one
 generation: selection / crossover / mutation kernels, the population pack,
 the fused fitness contraction (tensor cores, BF16 operands, FP32
 accumulation), the FP64 cross-tile error sum and the re-scoring of the 8 best
-candidates (FP32 products, FP64 sums) before the next elitism decision. The plain FP32 CUDA-core
+candidates (FP64, by the Gram form of the MSE) before the next elitism decision. The plain FP32 CUDA-core
 form of the same step is timed beside it, and a sample of chromosomes is
 re-scored by the FP64 oracle to state the accuracy of both.
 
@@ -573,7 +573,7 @@ def main():
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "basis": "chebyshev", "contraction": args.form,
                    "step": ("one generation: operators + pack + fused fitness + FP64 reduce"
-                            + (" + elite re-score (8 best: FP32 products, FP64 sums)"
+                            + (" + elite re-score (8 best: FP64 Gram form)"
                                if tensor else "")),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},

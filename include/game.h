@@ -136,12 +136,12 @@ int game_eval_fitness_prec(game_t h, const float* pop, int32_t P,
                            int32_t precision, double* fit_out);
 
 /* Elite re-scoring. The n best chromosomes of fit (by fitness, then lower
- * index; NaN ranks last) are evaluated again, and their entries of fit are
- * replaced: the expansion of Eq. 1 / Eq. 6 and the gene sums of Eq. 2 in FP32
- * (the arithmetic of GAME_PREC_FP32, relative error ~1e-7), the squared
- * residuals of Eq. 3 summed in FP64. Its purpose is the elitism decision of
- * Section 3 (2 elites, Section 5) when fit came from a reduced-precision
- * contraction: the best candidates are then ranked by accurate values.
+ * index; NaN ranks last) are evaluated again in FP64 by the Gram form of the
+ * MSE (see GAME_PREC_GRAM: exact to FP64 rounding; the handle builds its G
+ * on first use), and their entries of fit are replaced. Its purpose is the
+ * elitism decision of Section 3 (2 elites, Section 5) when fit came from a
+ * reduced-precision contraction: the best candidates are then ranked by
+ * accurate values.
  *   pop [P][K] FP32, fit [P] FP64 (in: any fitness vector of pop; out: the
  *   same with n entries replaced), both host or both device;
  *   1 <= n <= min(16, P); idx_out [n] (may be NULL; host or device) receives

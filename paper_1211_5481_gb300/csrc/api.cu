@@ -83,9 +83,6 @@ struct game_ctx {
   int* status = nullptr;   // device status word written by kernels
   // elite re-scoring
   int* cand = nullptr;
-  RescorePlan rplan{};
-  double* rpart = nullptr;
-  unsigned int* tickets = nullptr;
   // evaluation scratch, grown on demand
   int cap_P = 0;
   float* popT = nullptr;
@@ -97,6 +94,7 @@ struct game_ctx {
   double* G = nullptr;
   double* gb = nullptr;
   double* gyy = nullptr;
+  double* gpart = nullptr;    // re-scoring partial sums
   // FP8 column scales of the expansion (computed once, at the first FP8 use)
   unsigned int* colmax = nullptr;
   float* colscale = nullptr;
@@ -195,7 +193,9 @@ int ensure_gram(game_ctx* h) {
   double* phi = nullptr;
   double* part = nullptr;
   if (dev_alloc(&h->G, (size_t)K * K) != cudaSuccess || dev_alloc(&h->gb, (size_t)K) != cudaSuccess ||
-      dev_alloc(&h->gyy, 1) != cudaSuccess || dev_alloc(&phi, (size_t)rows * K) != cudaSuccess ||
+      dev_alloc(&h->gyy, 1) != cudaSuccess ||
+      dev_alloc(&h->gpart, (size_t)gram_small_parts(h->s) * kMaxRescore) != cudaSuccess ||
+      dev_alloc(&phi, (size_t)rows * K) != cudaSuccess ||
       dev_alloc(&part, (size_t)kGramSplits * K * K) != cudaSuccess) {
     cudaGetLastError();
     dev_free(phi);
@@ -303,7 +303,7 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
   cudaEvent_t t0;
   if (prec == GAME_PREC_GRAM) {
     t0 = stage_begin(h);
-    CK(launch_gram_fitness(h->s, dpop, P, h->G, h->gb, h->gyy, dfit, h->st));
+    CK(launch_gram_fitness(h->s, dpop, P, nullptr, h->G, h->gb, h->gyy, dfit, h->st));
     stage_end(h, t0, kFitness);
   } else if (prec == GAME_PREC_FP32) {
     const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
@@ -333,11 +333,16 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
   return GAME_OK;
 }
 
-// Enqueues the re-scoring of the n best entries of dfit (device arrays).
+int ensure_gram(game_ctx* h);
+
+// Enqueues the re-scoring of the n best entries of dfit (device arrays):
+// the candidates' FP64 fitness by the Gram form.
 int rescore_device(game_ctx* h, const float* dpop, int P, int n, double* dfit) {
+  int rc = ensure_gram(h);
+  if (rc) return rc;
   cudaEvent_t t0 = stage_begin(h);
-  CK(launch_rescore(h->rplan, h->s, h->Xt, h->y, dpop, P, n, dfit, h->cand, h->rpart,
-                    h->tickets, h->st));
+  CK(launch_select_top(dfit, P, n, h->cand, h->st));
+  CK(launch_gram_rescore(h->s, dpop, n, h->cand, h->G, h->gb, h->gyy, h->gpart, dfit, h->st));
   stage_end(h, t0, kRescore);
   return GAME_OK;
 }
@@ -546,8 +551,6 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->plan);
   dev_free(h->status);
   dev_free(h->cand);
-  dev_free(h->rpart);
-  dev_free(h->tickets);
   dev_free(h->popT);
   dev_free(h->popA);
   dev_free(h->a0);
@@ -555,6 +558,7 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->G);
   dev_free(h->gb);
   dev_free(h->gyy);
+  dev_free(h->gpart);
   dev_free(h->colmax);
   dev_free(h->colscale);
   dev_free(h->colinv);
@@ -653,7 +657,6 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) return bail(cuda_fail(e, "multiprocessor count"));
 
-  h->rplan = plan_rescore(s, h->num_sms);
   if (dev_alloc(&h->Xt, (size_t)s.Mpad * N) != cudaSuccess ||
       dev_alloc(&h->y, (size_t)s.Mpad) != cudaSuccess ||
       dev_alloc(&h->pop[0], (size_t)p.P * s.K) != cudaSuccess ||
@@ -661,9 +664,7 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
       dev_alloc(&h->fit, (size_t)p.P) != cudaSuccess ||
       dev_alloc(&h->plan, (size_t)p.P) != cudaSuccess ||
       dev_alloc(&h->status, 4) != cudaSuccess ||
-      dev_alloc(&h->cand, kMaxRescore) != cudaSuccess ||
-      dev_alloc(&h->rpart, (size_t)2 * h->rplan.grid * 8) != cudaSuccess ||
-      dev_alloc(&h->tickets, 2) != cudaSuccess) {
+      dev_alloc(&h->cand, kMaxRescore) != cudaSuccess) {
     cudaGetLastError();
     return bail(fail(GAME_ENOMEM, "device allocation of the training set / GA state"));
   }
@@ -687,7 +688,6 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
     dy = tmpy;
   }
   int bad_h[4] = {0, 0, 0, 0};
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->tickets, 0, 2 * sizeof(unsigned int), h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
   if (e == cudaSuccess) e = launch_relayout_X(dX, dy, s, h->Xt, h->y, h->status, h->st);
   if (e == cudaSuccess)

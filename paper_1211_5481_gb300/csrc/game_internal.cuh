@@ -23,9 +23,8 @@
 //   a0   [Ppad] FP32              bias genes.
 //   part [rows][Ppad] FP64        per-CTA partial sums of squared residuals.
 // Elite re-scoring (fixed size, allocated with the handle):
-//   cand [16] int32               candidate indices, best first.
-//   rpart [2][grid][8] FP64       per-CTA partial sums of the re-scored candidates.
-//   tickets [2] uint32            finish counters of the re-scoring CTAs (self-resetting).
+//   cand [16] int32               candidate indices, best first (re-scored by the
+//                                 Gram form, gram.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -113,13 +112,8 @@ cudaError_t prepare_fitness_batch(int smem_bytes);
 // launch only (capturable)
 cudaError_t launch_fitness_batch(const BatchArgs& a, int grid, int smem_bytes, cudaStream_t st);
 
-// rescore.cu
-struct RescorePlan { int pt, grid; };   // patterns per thread, CTAs per candidate group
-RescorePlan plan_rescore(const Shape& s, int num_sms);
-size_t rescore_smem_bytes(const Shape& s);
-cudaError_t launch_rescore(const RescorePlan& pl, const Shape& s, const float* Xt,
-                           const float* y, const float* pop, int P, int n, double* fit,
-                           int* cand, double* part, unsigned int* tickets, cudaStream_t st);
+// rescore.cu: the n best of fit (by (fit, index), NaN last) into cand [n]
+cudaError_t launch_select_top(const double* fit, int P, int n, int* cand, cudaStream_t st);
 // surrogate.cu -- the MLP fitness surrogate (K -> 256 -> 256 -> 1)
 constexpr int kSurrogateHidden = 256;
 constexpr float kAdamLr = 1e-3f, kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
@@ -166,9 +160,17 @@ int64_t gram_chunk_rows(const Shape& s);
 cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, double* G,
                               double* b, double* yy, double* phi_chunk, double* part,
                               cudaStream_t st);
-cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const double* G,
-                                const double* b, const double* yy, double* fit,
-                                cudaStream_t st);
+// fit of the P chromosomes pop [P][K] (idx NULL), or of rows idx[0..P-1]
+// written to fit[idx[p]]
+cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const int* idx,
+                                const double* G, const double* b, const double* yy,
+                                double* fit, cudaStream_t st);
+// the elite re-scoring: n <= kMaxRescore chromosomes pop rows idx[q], spread
+// over the GPU; part [gram_small_parts(s) * n] is scratch
+int gram_small_parts(const Shape& s);
+cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const int* idx,
+                                const double* G, const double* b, const double* yy,
+                                double* part, double* fit, cudaStream_t st);
 
 // api.cu
 void record_error(const char* msg);

@@ -161,18 +161,22 @@ __global__ void mirror_kernel(int K, double* __restrict__ G) {
   }
 }
 
-// fit_p = (yy - 2 a_p . b + a_p^T G a_p) / M for grp <= 8 chromosomes per CTA.
+// fit_p = (yy - 2 a_p . b + a_p^T G a_p) / M for grp <= 8 chromosomes per CTA;
+// with idx, entry p is chromosome idx[p] (read from pop row idx[p], written to
+// fit[idx[p]]).
 __global__ void __launch_bounds__(256)
 quad_kernel(int P, int K, int64_t M, int grp, const float* __restrict__ pop,
-            const double* __restrict__ G, const double* __restrict__ b,
-            const double* __restrict__ yy, double* __restrict__ fit) {
+            const int* __restrict__ idx, const double* __restrict__ G,
+            const double* __restrict__ b, const double* __restrict__ yy,
+            double* __restrict__ fit) {
   extern __shared__ double as[];   // [8][K] genes of the group, FP64 (rows >= grp zero)
   __shared__ double red[kQuadGroup][8];
   const int p0 = blockIdx.x * grp;
   const int ng = min(grp, P - p0);
   for (int e = threadIdx.x; e < grp * K; e += 256) {
     const int q = e / K, k = e % K;
-    as[e] = q < ng ? (double)pop[(int64_t)(p0 + q) * K + k] : 0.0;
+    const int64_t row = q < ng ? (idx ? idx[p0 + q] : p0 + q) : 0;
+    as[e] = q < ng ? (double)pop[row * K + k] : 0.0;
   }
   __syncthreads();
   double quad[kQuadGroup], lin[kQuadGroup];
@@ -212,8 +216,75 @@ quad_kernel(int P, int K, int64_t M, int grp, const float* __restrict__ pop,
   if (threadIdx.x < ng) {
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-    fit[p0 + threadIdx.x] = (*yy + s) / (double)M;
+    const int p = p0 + threadIdx.x;
+    fit[idx ? idx[p] : p] = (*yy + s) / (double)M;
   }
+}
+
+// Few chromosomes (n <= kMaxRescore; the elite re-scoring): the K x K
+// products are spread over the whole GPU. CTA (bx, by) owns rows
+// k1 in [128 bx, 128 bx + 128) (one per thread) and the k2-range
+// [by ks, (by + 1) ks) of sum_k2 G[k1][k2] a_q[k2] (G read column-wise, as
+// G[k2][k1]); each thread forms a_q[k1] h_q (and, in split 0,
+// -2 a_q[k1] b[k1]); the CTA's sum per candidate (lanes by xor-butterfly,
+// warps in order) goes to part[by][bx][q]. quad_small_finish adds the parts
+// in order and writes fit[idx[q]] = (yy + sum) / M.
+constexpr int kSmallRows = 128;
+__global__ void __launch_bounds__(kSmallRows)
+quad_small_kernel(int n, int K, int ks, const float* __restrict__ pop, const int* __restrict__ idx,
+                  const double* __restrict__ G, const double* __restrict__ b,
+                  double* __restrict__ part) {
+  extern __shared__ double av[];   // [n][ks] genes of the k2-range
+  __shared__ double red[kMaxRescore][kSmallRows / 32];
+  const int k1 = blockIdx.x * kSmallRows + threadIdx.x;
+  const int k2lo = blockIdx.y * ks, k2hi = min(K, k2lo + ks);
+  const int len = k2hi - k2lo;
+  for (int e = threadIdx.x; e < n * ks; e += kSmallRows) {
+    const int q = e / ks, c = e % ks;
+    av[e] = c < len ? (double)pop[(int64_t)idx[q] * K + k2lo + c] : 0.0;
+  }
+  __syncthreads();
+  double h[kMaxRescore];
+#pragma unroll
+  for (int q = 0; q < kMaxRescore; ++q) h[q] = 0.0;
+  if (k1 < K) {
+    for (int c = 0; c < len; ++c) {
+      const double g = G[(int64_t)(k2lo + c) * K + k1];
+#pragma unroll
+      for (int q = 0; q < kMaxRescore; ++q)
+        if (q < n) h[q] = fma(g, av[q * ks + c], h[q]);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kMaxRescore; ++q) {
+    if (q >= n) break;
+    double v = 0.0;
+    if (k1 < K) {
+      const double ak = pop[(int64_t)idx[q] * K + k1];
+      v = ak * h[q];
+      if (blockIdx.y == 0) v -= 2.0 * ak * b[k1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    double sum = 0.0;
+    for (int w = 0; w < kSmallRows / 32; ++w) sum += red[threadIdx.x][w];
+    part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * n + threadIdx.x] = sum;
+  }
+}
+
+__global__ void quad_small_finish(int n, int nparts, int64_t M, const int* __restrict__ idx,
+                                  const double* __restrict__ part, const double* __restrict__ yy,
+                                  double* __restrict__ fit) {
+  const int q = threadIdx.x;
+  if (q >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < nparts; ++j) s += part[(int64_t)j * n + q];
+  fit[idx[q]] = (*yy + s) / (double)M;
 }
 
 int blocks_for(int64_t n) {
@@ -258,9 +329,36 @@ cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const double* G,
-                                const double* b, const double* yy, double* fit,
-                                cudaStream_t st) {
+int gram_small_parts(const Shape& s) {
+  const int bx = (s.K + kSmallRows - 1) / kSmallRows;
+  int by = (304 + bx - 1) / bx;   // about two CTAs per SM over the grid
+  if (by > s.K) by = s.K;
+  return bx * by;
+}
+
+cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const int* idx,
+                                const double* G, const double* b, const double* yy,
+                                double* part, double* fit, cudaStream_t st) {
+  if (n < 1 || n > kMaxRescore) return cudaErrorInvalidValue;
+  const int bx = (s.K + kSmallRows - 1) / kSmallRows;
+  const int by = gram_small_parts(s) / bx;
+  const int ks = (s.K + by - 1) / by;
+  const size_t smem = (size_t)n * ks * sizeof(double);   // <= 16 x 410 x 8 at K = 4097
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        quad_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  quad_small_kernel<<<dim3(bx, by), kSmallRows, smem, st>>>(n, s.K, ks, pop, idx, G, b, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  quad_small_finish<<<1, 32, 0, st>>>(n, bx * by, s.M, idx, part, yy, fit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const int* idx,
+                                const double* G, const double* b, const double* yy,
+                                double* fit, cudaStream_t st) {
   // as many chromosomes per CTA (<= 8) as fit in 200 KB of FP64 genes
   int grp = (int)((200 * 1024) / ((size_t)s.K * sizeof(double)));
   if (grp > kQuadGroup) grp = kQuadGroup;
@@ -269,7 +367,8 @@ cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const d
   cudaError_t e = cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024);
   if (e != cudaSuccess) return e;
-  quad_kernel<<<(P + grp - 1) / grp, 256, smem, st>>>(P, s.K, s.M, grp, pop, G, b, yy, fit);
+  quad_kernel<<<(P + grp - 1) / grp, 256, smem, st>>>(P, s.K, s.M, grp, pop, idx, G, b, yy,
+                                                       fit);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ _lib = None
 
 CHEB, TRIG = 0, 1
 ERR_MSE, ERR_RMSE, ERR_MAE = 0, 1, 2
+SEL_TOURNAMENT, SEL_RANKING, SEL_ROULETTE = 0, 1, 2
 
 
 class GAParams(ctypes.Structure):
@@ -35,14 +36,17 @@ class GAParams(ctypes.Structure):
         ("thr_pm", ctypes.c_uint32),
         ("sigma", ctypes.c_float),
         ("immigrants", ctypes.c_int32),
+        ("selection", ctypes.c_int32),
     ]
 
 
-def ga_params(elitism=2, tournament=3, pc=0.9, pm=0.02, sigma=0.1, immigrants=0):
+def ga_params(elitism=2, tournament=3, pc=0.9, pm=0.02, sigma=0.1, immigrants=0,
+              selection=SEL_TOURNAMENT):
     """Operator parameters; the rates become 24-bit integer thresholds
     floor(rate * 2^24), computed once in FP64."""
     return GAParams(elitism, tournament, int(np.floor(pc * 2.0**24)),
-                    int(np.floor(pm * 2.0**24)), float(np.float32(sigma)), immigrants)
+                    int(np.floor(pm * 2.0**24)), float(np.float32(sigma)), immigrants,
+                    selection)
 
 
 def build(force: bool = False) -> str:

@@ -24,10 +24,12 @@
  *  - Fitness is the MSE (Section 3 after Eq. 3; Section 5), minimised; ties
  *    are broken by the lower index and a NaN fitness ranks as +infinity.
  *  - The operators are named (Section 3: crossover, mutation, elitism;
- *    Section 5: rates and 2 elites) but not defined. The definitions below
- *    (tournament selection, one-point crossover, per-gene Gaussian mutation
+ *    Section 5: rates, 2 elites, ranking and roulette selection) but not
+ *    defined. The definitions below (tournament, linear-ranking and
+ *    roulette selection, one-point crossover, per-gene Gaussian mutation
  *    with an Irwin-Hall normal, clamp to [-1, 1], counter-based Philox
- *    draws) are this project's.
+ *    draws) are this project's. Roulette turns on 1 / (1 + fit), a
+ *    positive transform that is larger for a better (smaller) MSE.
  *  - Section 4 replaces older individuals by fresh random chromosomes each
  *    generation, without a count: `immigrants` slots at the end of the
  *    population are refilled (0 by default).
@@ -298,6 +300,67 @@ static float irwin_hall_12(uint64_t seed, uint32_t g, uint32_t s, uint32_t k) {
   return centred * (1.0f / 16777216.0f);
 }
 
+/* Roulette weight of a fitness value (lower fitness is better, so the wheel
+ * turns on the maximised transform 1 / (1 + fit)): the integer
+ * floor(2^32 * (1 / (1 + fit))) with FP64 rounding of the sum and the
+ * quotient; 0 for a NaN, negative or infinite fitness. */
+static uint64_t roulette_weight(double f) {
+  if (!(f >= 0.0) || isinf(f)) return 0;
+  const double w = 1.0 / (1.0 + f);
+  return (uint64_t)(w * 4294967296.0);
+}
+
+/* Selection tables over the P current chromosomes: for ranking, order[r] =
+ * the chromosome of rank r (0 = best); for roulette, the weights and their
+ * total. */
+typedef struct {
+  int32_t* order;
+  uint64_t* weight;
+  uint64_t total;
+} selection_tables;
+
+/* Parent r (0 or 1) of pair q. Every mode takes its random words from
+ * Philox(seed; g, q, r, TOUR | call << 8). */
+static int32_t select_parent(const double* fit, int32_t P, const oracle_ga_params* prm,
+                             const selection_tables* tab, uint64_t seed, uint32_t g,
+                             uint32_t q, uint32_t r) {
+  uint32_t w[4];
+  if (prm->selection == ORACLE_SEL_RANKING) {
+    /* u uniform on [0, W), W = P (P + 1) / 2; rank k covers the u with
+     * sum_{j<k} (P - j) <= u < sum_{j<=k} (P - j). */
+    draw(seed, g, q, r, TAG_TOUR, w);
+    const uint64_t u = ((uint64_t)w[0] * tab->total) >> 32;
+    uint64_t cum = 0;
+    for (int32_t k = 0; k < P; ++k) {
+      cum += (uint64_t)(P - k);
+      if (u < cum) return tab->order[k];
+    }
+    return tab->order[P - 1];
+  }
+  if (prm->selection == ORACLE_SEL_ROULETTE) {
+    /* u uniform on [0, W) from 64 random bits, W = sum of the weights;
+     * chromosome p covers [sum_{j<p} w_j, sum_{j<=p} w_j). */
+    draw(seed, g, q, r, TAG_TOUR, w);
+    if (tab->total == 0) return (int32_t)(((uint64_t)w[0] * (uint64_t)P) >> 32);
+    const uint64_t bits = ((uint64_t)w[0] << 32) | w[1];
+    const uint64_t u = (uint64_t)(((unsigned __int128)bits * tab->total) >> 64);
+    uint64_t cum = 0;
+    for (int32_t p = 0; p < P; ++p) {
+      cum += tab->weight[p];
+      if (u < cum) return p;
+    }
+    return P - 1;
+  }
+  /* tournament: the best of T uniform candidates */
+  int32_t win = -1;
+  for (int32_t s = 0; s < prm->tournament; ++s) {
+    if (s % 4 == 0) draw(seed, g, q, r, TAG_TOUR | ((uint32_t)(s / 4) << 8), w);
+    const int32_t c = (int32_t)(((uint64_t)w[s % 4] * (uint64_t)P) >> 32);
+    if (win < 0 || better(fit[c], c, fit[win], win)) win = c;
+  }
+  return win;
+}
+
 int oracle_generation(const float* pop, const double* fit, int32_t P,
                       int32_t K, const oracle_ga_params* prm, uint64_t seed,
                       uint32_t g, float* next) {
@@ -310,10 +373,38 @@ int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
   if (!pop || !fit || !next || !prm || K < 1) return -1;
   const int32_t E = prm->elitism, T = prm->tournament, I = prm->immigrants;
   if (E < 0 || T < 1 || I < 0 || P < E + I + 2 || n_out < E + I + 2) return -1;
+  if (prm->selection < ORACLE_SEL_TOURNAMENT || prm->selection > ORACLE_SEL_ROULETTE) return -1;
+  if (prm->selection == ORACLE_SEL_RANKING && P > 65535) return -1;
+
+  /* 0. Selection tables (ranking: the order by (fitness, index), each
+   * chromosome's rank counted as the number that beat it; roulette: the
+   * weights). */
+  selection_tables tab = {NULL, NULL, 0};
+  if (prm->selection == ORACLE_SEL_RANKING) {
+    tab.order = (int32_t*)malloc(sizeof(int32_t) * (size_t)P);
+    if (!tab.order) return -2;
+    for (int32_t p = 0; p < P; ++p) {
+      int32_t rank = 0;
+      for (int32_t q = 0; q < P; ++q) rank += better(fit[q], q, fit[p], p);
+      tab.order[rank] = p;
+    }
+    tab.total = (uint64_t)P * (uint64_t)(P + 1) / 2;
+  } else if (prm->selection == ORACLE_SEL_ROULETTE) {
+    tab.weight = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)P);
+    if (!tab.weight) return -2;
+    for (int32_t p = 0; p < P; ++p) {
+      tab.weight[p] = roulette_weight(fit[p]);
+      tab.total += tab.weight[p];
+    }
+  }
 
   /* 1. Elitism: the E best by (fitness, index) are copied unchanged. */
   int32_t* chosen = (int32_t*)calloc((size_t)P, sizeof(int32_t));
-  if (!chosen) return -2;
+  if (!chosen) {
+    free(tab.order);
+    free(tab.weight);
+    return -2;
+  }
   for (int32_t e = 0; e < E; ++e) {
     int32_t best = -1;
     for (int32_t p = 0; p < P; ++p)
@@ -324,23 +415,13 @@ int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
   }
   free(chosen);
 
-  /* 2.-3. Pairs of tournament winners (drawn from the P current
-   * chromosomes), one-point crossover, children in slots E.. n_out-1. */
+  /* 2.-3. Pairs of parents selected from the P current chromosomes,
+   * one-point crossover, children in slots E.. n_out-1. */
   const int32_t npairs = (n_out - E + 1) / 2;
   for (int32_t q = 0; q < npairs; ++q) {
     int32_t parent[2];
-    for (int r = 0; r < 2; ++r) {
-      int32_t win = -1;
-      uint32_t w[4];
-      for (int32_t s = 0; s < T; ++s) {
-        if (s % 4 == 0)
-          draw(seed, g, (uint32_t)q, (uint32_t)r,
-               TAG_TOUR | ((uint32_t)(s / 4) << 8), w);
-        const int32_t c = (int32_t)(((uint64_t)w[s % 4] * (uint64_t)P) >> 32);
-        if (win < 0 || better(fit[c], c, fit[win], win)) win = c;
-      }
-      parent[r] = win;
-    }
+    for (int r = 0; r < 2; ++r)
+      parent[r] = select_parent(fit, P, prm, &tab, seed, g, (uint32_t)q, (uint32_t)r);
     uint32_t w[4];
     draw(seed, g, (uint32_t)q, 0u, TAG_XO, w);
     int32_t cut = K; /* no crossover: children are copies of the parents */
@@ -379,6 +460,8 @@ int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
       draw(seed, g, (uint32_t)s, (uint32_t)k, TAG_IMM, w);
       next[(int64_t)s * K + k] = uniform_gene(w[0]);
     }
+  free(tab.order);
+  free(tab.weight);
   return 0;
 }
 

@@ -27,6 +27,7 @@ extern "C" {
 
 enum { ORACLE_CHEB = 0, ORACLE_TRIG = 1 };
 enum { ORACLE_ERR_MSE = 0, ORACLE_ERR_RMSE = 1, ORACLE_ERR_MAE = 2 };
+enum { ORACLE_SEL_TOURNAMENT = 0, ORACLE_SEL_RANKING = 1, ORACLE_SEL_ROULETTE = 2 };
 
 /* Section 3, Eq. 4: population size B*N + 1. */
 int64_t oracle_num_chromosomes(int32_t N, int32_t basis);
@@ -75,7 +76,15 @@ int oracle_fitness_gram(const double* G, const double* b, double yy, int64_t M,
 void oracle_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4],
                           uint32_t out[4]);
 
-/* GA operator parameters. thr_pc = floor(pc * 2^24), thr_pm = floor(pm * 2^24). */
+/* GA operator parameters. thr_pc = floor(pc * 2^24), thr_pm = floor(pm * 2^24).
+ * selection (Section 5 names roulette and ranking selection):
+ *  ORACLE_SEL_TOURNAMENT: the best of `tournament` uniform draws;
+ *  ORACLE_SEL_RANKING: linear ranking, rank r (0 = best by (fitness, index))
+ *    drawn with weight P - r (needs P <= 65535);
+ *  ORACLE_SEL_ROULETTE: fitness-proportionate on the maximised transform
+ *    1 / (1 + fit), as the integer weight floor(2^32 RN(1 / RN(1 + fit)))
+ *    (0 for a NaN, negative or infinite fit; uniform draws when every
+ *    weight is 0). */
 typedef struct {
   int32_t elitism;     /* E */
   int32_t tournament;  /* candidates per tournament */
@@ -83,14 +92,15 @@ typedef struct {
   uint32_t thr_pm;
   float sigma;         /* Gaussian mutation step */
   int32_t immigrants;  /* fresh random chromosomes per generation */
+  int32_t selection;   /* ORACLE_SEL_* */
 } oracle_ga_params;
 
 /* Gene initialisation, uniform in [-1, 1) (Section 3: genes generated at
  * random, normalised between -1 and +1). pop[P][K]. */
 int oracle_init_population(uint64_t seed, int32_t P, int32_t K, float* pop);
 
-/* One generation g -> g+1 (elitism, tournament selection, one-point
- * crossover, Gaussian mutation, clamp to [-1, 1]). pop[P][K], fit[P],
+/* One generation g -> g+1 (elitism, selection, one-point crossover,
+ * Gaussian mutation, clamp to [-1, 1]). pop[P][K], fit[P],
  * next[P][K]; next must not alias pop. */
 int oracle_generation(const float* pop, const double* fit, int32_t P,
                       int32_t K, const oracle_ga_params* prm, uint64_t seed,
@@ -111,7 +121,7 @@ int oracle_rescore(const double* X, const double* y, int64_t M, int32_t N,
 
 /* The operators of oracle_generation with n_out output slots instead of P
  * (oversampled offspring): slots 0..E-1 the elites, E..n_out-1 children of
- * tournaments drawn from the P current chromosomes, the last I slots
+ * parents selected from the P current chromosomes, the last I slots
  * immigrants; next[n_out][K]. n_out = P is oracle_generation. */
 int oracle_offspring(const float* pop, const double* fit, int32_t P, int32_t K,
                      const oracle_ga_params* prm, uint64_t seed, uint32_t g,

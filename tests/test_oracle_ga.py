@@ -247,3 +247,88 @@ def test_mutation_clamps_both_ends(orc):
     # moved inwards
     assert np.count_nonzero(np.abs(child) == 1.0) > 0.3 * child.size
     assert np.count_nonzero(np.abs(child) < 1.0) > 0.3 * child.size
+
+
+def _parent_counts(orc, fit, selection, n_out, seeds=(5,), g=0):
+    """Selection frequencies: with no crossover, mutation, elites or
+    immigrants each child slot is a copy of one selected parent, identified
+    by gene 0."""
+    P = fit.size
+    pop = np.zeros((P, 3), dtype=np.float32)
+    pop[:, 0] = np.arange(P) / 2.0**20
+    prm = orc.ga_params(elitism=0, pc=0.0, pm=0.0, selection=selection)
+    counts = np.zeros(P)
+    for seed in seeds:
+        nxt = orc.offspring(pop, fit, seed, g, n_out, prm)
+        counts += np.bincount((nxt[:, 0] * 2.0**20).round().astype(int), minlength=P)
+    return counts
+
+
+def _within_binomial(counts, prob, z=5.0):
+    n = counts.sum()
+    sd = np.sqrt(n * prob * (1 - prob))
+    return np.all(np.abs(counts - n * prob) <= z * sd + 1e-9)
+
+
+def test_ranking_selection_is_linear_in_rank(orc):
+    """Linear ranking: the member of rank r (0 = best) is drawn with
+    probability (P - r) / (P (P + 1) / 2), whatever the fitness values."""
+    P = 7
+    fit = np.array([0.3, 5.0, 0.1, 2.0, 0.2, 9.0, 1.0])   # ranks 2 5 0 4 1 6 3
+    rank = np.argsort(np.argsort(fit))
+    counts = _parent_counts(orc, fit, orc.SEL_RANKING, 60000)
+    prob = (P - rank) / (P * (P + 1) / 2)
+    assert _within_binomial(counts, prob)
+    # only the ranks matter: a monotone transform of fit draws the same parents
+    np.testing.assert_array_equal(counts, _parent_counts(orc, np.exp(fit), orc.SEL_RANKING, 60000))
+
+
+def test_ranking_ties_and_nan(orc):
+    """Equal fitness ranks by index; NaN ranks last (weight 1)."""
+    fit = np.array([1.0, 1.0, 1.0, np.nan])
+    counts = _parent_counts(orc, fit, orc.SEL_RANKING, 40000)
+    assert _within_binomial(counts, np.array([4, 3, 2, 1]) / 10.0)
+
+
+def test_roulette_selection_is_proportional(orc):
+    """Roulette on 1 / (1 + fit): probability proportional to it; NaN and
+    infinite fitness are never drawn."""
+    fit = np.array([0.0, 1.0, 3.0, 9.0, np.nan, np.inf, 0.5])
+    w = np.where(np.isfinite(fit), 1.0 / (1.0 + np.nan_to_num(fit, nan=0.0)), 0.0)
+    counts = _parent_counts(orc, fit, orc.SEL_ROULETTE, 60000)
+    assert counts[4] == 0 and counts[5] == 0
+    assert _within_binomial(counts, w / w.sum())
+
+
+def test_roulette_all_zero_weights_is_uniform(orc):
+    fit = np.full(5, np.nan)
+    counts = _parent_counts(orc, fit, orc.SEL_ROULETTE, 50000)
+    assert _within_binomial(counts, np.full(5, 0.2))
+
+
+def test_roulette_large_fitness_spread(orc):
+    """A fitness of 1e12 has the integer weight floor(2^32 / (1 + 1e12)) = 0,
+    so it is never drawn next to fit = 0 (weight 2^32)."""
+    fit = np.array([1e12, 0.0])
+    counts = _parent_counts(orc, fit, orc.SEL_ROULETTE, 2000)
+    assert counts[0] == 0 and counts[1] == 2000
+
+
+@pytest.mark.parametrize("selection", [1, 2])
+def test_selection_modes_keep_invariants(orc, selection):
+    """Elites verbatim, population size, genes in range, under every mode."""
+    P, K, E = 33, 11, 2
+    rng = np.random.default_rng(selection)
+    pop = orc.init_population(3, P, K)
+    fit = rng.uniform(0, 1, P)
+    prm = orc.ga_params(elitism=E, selection=selection)
+    nxt = orc.generation(pop, fit, 9, 1, prm)
+    assert nxt.shape == pop.shape and np.all(np.abs(nxt) <= 1)
+    for e, src in enumerate(_elites(fit, E)):
+        np.testing.assert_array_equal(nxt[e], pop[src])
+
+
+def test_selection_rejects_bad_mode(orc):
+    pop = orc.init_population(1, 4, 5)
+    with pytest.raises(ValueError):
+        orc.generation(pop, np.zeros(4), 1, 0, orc.ga_params(elitism=0, selection=3))

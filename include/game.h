@@ -15,6 +15,13 @@
  *
  * Fitness is the mean squared error of Eq. 3 over all M patterns
  * (Section 3; Section 5 sets MSE as the error function), lower is better.
+ * Also offered (game_params.error): its square root (RMSE) and the mean
+ * absolute difference (MAE), the other errors Section 3 names.
+ *
+ * Shared genes (game_params.tied = 1): Eq. 2 as printed indexes the genes by
+ * basis group and degree only, common to every feature, so a chromosome has
+ * K = B*d + 1 genes (Eq. 5): gene 0 is a_0 and gene 1 + b*d + (j-1) weights
+ * sum_i phi_{b,j}(x_i). Every K below is then B*d + 1.
  *
  * Conventions for every call:
  *  - Returns GAME_OK (0) or a negative GAME_E* code; game_last_error()
@@ -46,6 +53,24 @@ extern "C" {
 
 #define GAME_BASIS_CHEB 0
 #define GAME_BASIS_TRIG 1
+
+/* Error function of the fitness (game_params.error). */
+#define GAME_ERR_MSE 0     /* (1/M) sum_m (y_m - Out(m))^2 (Eq. 3, averaged) */
+#define GAME_ERR_RMSE 1    /* sqrt of the MSE */
+#define GAME_ERR_MAE 2     /* (1/M) sum_m |y_m - Out(m)| */
+
+/* Parent selection (game_params.selection; Section 5 names ranking and
+ * roulette). Each parent takes its random words from one Philox4x32-10
+ * call (counter: generation, pair, parent, purpose). */
+#define GAME_SEL_TOURNAMENT 0 /* best of `tournament` uniform draws */
+#define GAME_SEL_RANKING 1    /* linear ranking: the chromosome of rank r
+                                 (0 = best by fitness, then lower index;
+                                 NaN last) drawn with weight P - r;
+                                 P <= 16384 */
+#define GAME_SEL_ROULETTE 2   /* fitness-proportionate on 1 / (1 + fit):
+                                 integer weight floor(2^32 RN(1/RN(1 + fit))),
+                                 0 for NaN or infinite fit; uniform draws
+                                 when every weight is 0 */
 
 /* Arithmetic of the fitness contraction (the expansion-times-genes sum). In
  * every form the residuals of Eq. 3 are squared in FP32 and the sum over
@@ -100,10 +125,18 @@ typedef struct {
                            surrogate (game_surrogate_*), 0: off */
   int32_t oversample;   /* offspring per kept child when screening (>= 1,
                            oversample * (P - elitism) <= 16384) */
-  int32_t reserved[5];  /* must be zero */
+  int32_t selection;    /* GAME_SEL_* (default tournament) */
+  int32_t tied;         /* 1: shared genes, K = B*d + 1 (Eq. 2 as printed,
+                           Eq. 5); 0: one gene per feature, basis group and
+                           degree, K = B*N*d + 1 (default) */
+  int32_t error;        /* GAME_ERR_* (default MSE). GAME_ERR_MAE has no
+                           Gram form: it needs a direct precision
+                           (not GAME_PREC_GRAM) and rescore_top = 0 */
+  int32_t reserved[2];  /* must be zero */
 } game_params;
 
-/* Fills *out with the defaults listed above (and rescore_top = 8). */
+/* Fills *out with the defaults listed above (and rescore_top = 8,
+ * oversample = 8, tournament selection, per-feature genes, MSE). */
 int game_params_default(game_params* out);
 
 /* Creates a handle for one training set and copies it to the device.
@@ -124,7 +157,8 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N,
 /* Shape queries. */
 int game_get_shape(game_t h, int64_t* M, int32_t* N, int32_t* K, int32_t* P);
 
-/* Fitness of a caller-supplied population (Eq. 2, Eq. 3, MSE):
+/* Fitness of a caller-supplied population (Eq. 2, Eq. 3; the handle's
+ * error function):
  *   pop [P][K] FP32 genes, fit_out [P] FP64, both host or both device.
  * P >= 1 may differ from the handle's population size. Uses the handle's
  * precision. Does not touch the handle's GA state. */
@@ -146,12 +180,14 @@ int game_eval_fitness_prec(game_t h, const float* pop, int32_t P,
  *   same with n entries replaced), both host or both device;
  *   1 <= n <= min(16, P); idx_out [n] (may be NULL; host or device) receives
  *   the candidates' indices, best first.
+ * With GAME_ERR_RMSE the replaced entries are the square roots of the
+ * Gram-form MSE; GAME_ERR_MAE handles refuse (GAME_EINVAL).
  * Entries other than the n candidates are not modified. Host arguments
  * synchronise; device arguments only enqueue. */
 int game_rescore_top(game_t h, const float* pop, int32_t P, double* fit,
                      int32_t n, int32_t* idx_out);
 
-/* One generation g -> g+1 of the GA state: elitism, tournament selection,
+/* One generation g -> g+1 of the GA state: elitism, parent selection,
  * one-point crossover, per-gene Gaussian mutation, clamping to [-1, 1]
  * (Section 3 names the operators; Section 5 the rates), then the fitness of
  * the new population. All random decisions come from Philox4x32-10 keyed
@@ -296,7 +332,8 @@ typedef struct {
  * the widest that fits. Fitness values depend on the tile width in their
  * last bits (FP32 sums inside a tile): pass the widths game_batch_get_tiles
  * returns to reproduce a run exactly. Validation as game_create per run
- * (GAME_EINVAL naming the run), plus K - 1 <= 2048 and N <= 256. The initial
+ * (GAME_EINVAL naming the run), plus K - 1 <= 2048 and N <= 256; batched
+ * runs use tournament selection, per-feature genes and the MSE. The initial
  * populations are generated and evaluated. Synchronous. */
 int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* prm,
                       const int32_t* tiles, int32_t autotune, void* cuda_stream,
@@ -318,7 +355,9 @@ int game_batch_sync(game_batch_t b);
 int game_batch_destroy(game_batch_t b);
 
 /* The Gram form's G [K][K], b [K] and y.y (FP64; built on first use; any
- * output may be NULL; host or device). Synchronises. */
+ * output may be NULL; host or device). For a shared-gene handle the
+ * expansion is psi_{b,j}(x) = sum_i phi_{b,j}(x_i) (K = B*d + 1).
+ * Synchronises. */
 int game_gram(game_t h, double* G_out, double* b_out, double* yy_out);
 
 /* Waits for the handle's stream and reports a kernel timeout, if any. */

@@ -67,7 +67,8 @@ void dev_free(void* p) {
 }  // namespace
 
 struct game_ctx {
-  Shape s{};
+  Shape s{};     // contraction shape: K = B*N*d + 1 expansion columns (with the bias)
+  int Kg = 0;    // genes per chromosome: s.K, or B*d + 1 with shared genes
   game_params prm{};
   cudaStream_t st = nullptr;
   int device = 0;
@@ -83,6 +84,12 @@ struct game_ctx {
   int* status = nullptr;   // device status word written by kernels
   // elite re-scoring
   int* cand = nullptr;
+  // selection tables (ranking order, roulette weight sums)
+  int* sel_order = nullptr;
+  uint64_t* sel_cum = nullptr;
+  // shared genes: the population replicated over features, [P][s.K]
+  float* rpop = nullptr;
+  size_t rpop_cap = 0;
   // evaluation scratch, grown on demand
   int cap_P = 0;
   float* popT = nullptr;
@@ -186,15 +193,26 @@ bool valid_precision(int prec) {
 
 // G, b, yy of the training set (FP64), once per handle; the build's scratch
 // (a chunk of the FP64 design matrix and split partial sums) is released.
+// Shape of the Gram form: the chromosome's genes (the shared-gene expansion
+// psi for a tied handle).
+Shape gram_shape(const game_ctx* h) {
+  Shape g = h->s;
+  g.K = h->Kg;
+  g.Kp = h->Kg - 1;
+  g.tied = h->prm.tied;
+  return g;
+}
+
 int ensure_gram(game_ctx* h) {
   if (h->G) return GAME_OK;
-  const int K = h->s.K;
-  const int64_t rows = gram_chunk_rows(h->s);
+  const int K = h->Kg;
+  const Shape gs = gram_shape(h);
+  const int64_t rows = gram_chunk_rows(gs);
   double* phi = nullptr;
   double* part = nullptr;
   if (dev_alloc(&h->G, (size_t)K * K) != cudaSuccess || dev_alloc(&h->gb, (size_t)K) != cudaSuccess ||
       dev_alloc(&h->gyy, 1) != cudaSuccess ||
-      dev_alloc(&h->gpart, (size_t)gram_small_parts(h->s) * kMaxRescore) != cudaSuccess ||
+      dev_alloc(&h->gpart, (size_t)gram_small_parts(gs) * kMaxRescore) != cudaSuccess ||
       dev_alloc(&phi, (size_t)rows * K) != cudaSuccess ||
       dev_alloc(&part, (size_t)kGramSplits * K * K) != cudaSuccess) {
     cudaGetLastError();
@@ -207,7 +225,7 @@ int ensure_gram(game_ctx* h) {
     h->gb = h->gyy = nullptr;
     return fail(GAME_ENOMEM, "Gram matrix");
   }
-  cudaError_t e = launch_gram_build(h->s, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->st);
+  cudaError_t e = launch_gram_build(gs, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dev_free(phi);
   dev_free(part);
@@ -295,26 +313,58 @@ int ensure_scratch(game_ctx* h, int P, int prec) {
   return GAME_OK;
 }
 
-// Enqueues the fitness of a device population dpop [P][K] into dfit [P].
+// The shared-gene population dpop [P][Kg] replicated over the features into
+// h->rpop [P][s.K] for the direct forms.
+int replicate_tied(game_ctx* h, const float* dpop, int P) {
+  const size_t need = (size_t)P * h->s.K;
+  if (need > h->rpop_cap) {
+    dev_free(h->rpop);
+    h->rpop = nullptr;
+    h->rpop_cap = 0;
+    if (dev_alloc(&h->rpop, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GAME_ENOMEM, "replicated population");
+    }
+    h->rpop_cap = need;
+  }
+  cudaEvent_t t0 = stage_begin(h);
+  CK(launch_replicate_tied(dpop, P, h->s, h->rpop, h->st));
+  stage_end(h, t0, kPack);
+  return GAME_OK;
+}
+
+// Enqueues the fitness of a device population dpop [P][Kg] into dfit [P].
 int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
+  const int err = h->prm.error;
+  if (prec == GAME_PREC_GRAM && err == GAME_ERR_MAE)
+    return fail(GAME_EINVAL, "the MAE has no Gram form");
   int rc = ensure_scratch(h, P, prec);
   if (rc) return rc;
   const int Ppad = ceil_div(P, 128) * 128;
   cudaEvent_t t0;
   if (prec == GAME_PREC_GRAM) {
     t0 = stage_begin(h);
-    CK(launch_gram_fitness(h->s, dpop, P, nullptr, h->G, h->gb, h->gyy, dfit, h->st));
+    CK(launch_gram_fitness(gram_shape(h), dpop, P, nullptr, h->G, h->gb, h->gyy, dfit, err,
+                           h->st));
     stage_end(h, t0, kFitness);
-  } else if (prec == GAME_PREC_FP32) {
+    return GAME_OK;
+  }
+  if (h->prm.tied) {
+    rc = replicate_tied(h, dpop, P);
+    if (rc) return rc;
+    dpop = h->rpop;
+  }
+  if (prec == GAME_PREC_FP32) {
     const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
     t0 = stage_begin(h);
     CK(launch_pack_fp32(dpop, P, Ppad, h->s, pl.Kc, h->popT, h->a0, h->st));
     stage_end(h, t0, kPack);
     t0 = stage_begin(h);
-    CK(launch_fitness_fp32(pl, h->s, h->Xt, h->y, h->popT, h->a0, P, Ppad, h->part, h->st));
+    CK(launch_fitness_fp32(pl, h->s, h->Xt, h->y, h->popT, h->a0, P, Ppad, h->part, err,
+                           h->st));
     stage_end(h, t0, kFitness);
     t0 = stage_begin(h);
-    CK(launch_reduce(h->part, pl.grid_y, P, Ppad, h->s.M, dfit, h->st));
+    CK(launch_reduce(h->part, pl.grid_y, P, Ppad, h->s.M, err, dfit, h->st));
     stage_end(h, t0, kReduce);
   } else {
     const TcPlan pl = plan_tc(h->s, P, h->num_sms, tc_form(prec));
@@ -324,10 +374,10 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
     stage_end(h, t0, kPack);
     t0 = stage_begin(h);
     CK(launch_fitness_tc(pl, h->s, h->Xt, h->y, h->popA, h->a0, h->uscale, h->colinv, P, Ppad,
-                         h->part, h->status, h->st));
+                         h->part, h->status, err, h->st));
     stage_end(h, t0, kFitness);
     t0 = stage_begin(h);
-    CK(launch_reduce(h->part, pl.rows, P, Ppad, h->s.M, dfit, h->st));
+    CK(launch_reduce(h->part, pl.rows, P, Ppad, h->s.M, err, dfit, h->st));
     stage_end(h, t0, kReduce);
   }
   return GAME_OK;
@@ -338,11 +388,13 @@ int ensure_gram(game_ctx* h);
 // Enqueues the re-scoring of the n best entries of dfit (device arrays):
 // the candidates' FP64 fitness by the Gram form.
 int rescore_device(game_ctx* h, const float* dpop, int P, int n, double* dfit) {
+  if (h->prm.error == GAME_ERR_MAE) return fail(GAME_EINVAL, "the MAE has no Gram form to re-score with");
   int rc = ensure_gram(h);
   if (rc) return rc;
   cudaEvent_t t0 = stage_begin(h);
   CK(launch_select_top(dfit, P, n, h->cand, h->st));
-  CK(launch_gram_rescore(h->s, dpop, n, h->cand, h->G, h->gb, h->gyy, h->gpart, dfit, h->st));
+  CK(launch_gram_rescore(gram_shape(h), dpop, n, h->cand, h->G, h->gb, h->gyy, h->gpart, dfit,
+                         h->prm.error, h->st));
   stage_end(h, t0, kRescore);
   return GAME_OK;
 }
@@ -363,13 +415,13 @@ int eval_state(game_ctx* h) {
 int ensure_surrogate(game_ctx* h, int rows) {
   SurrogateDev& s = h->sd;
   if (!h->sd_params) {
-    const int64_t n = surrogate_param_count(h->s.K);
-    s.K = h->s.K;
+    const int64_t n = surrogate_param_count(h->Kg);
+    s.K = h->Kg;
     if (dev_alloc(&s.w, n) != cudaSuccess || dev_alloc(&s.g, n) != cudaSuccess ||
         dev_alloc(&s.m, n) != cudaSuccess || dev_alloc(&s.v, n) != cudaSuccess ||
         dev_alloc(&s.loss, 1) != cudaSuccess || dev_alloc(&s.tstat, 2) != cudaSuccess ||
         dev_alloc(&s.split_ws, (size_t)kMaxSplits * kSurrogateHidden *
-                                   (h->s.K > kSurrogateHidden ? h->s.K : kSurrogateHidden)) !=
+                                   (h->Kg > kSurrogateHidden ? h->Kg : kSurrogateHidden)) !=
             cudaSuccess) {
       cudaGetLastError();
       return fail(GAME_ENOMEM, "surrogate parameters");
@@ -417,7 +469,7 @@ int surrogate_step(game_ctx* h, const float* X, const double* fit, int n) {
 // Adds the current population and its exact fitness to the replay ring and
 // trains one step on each stored generation, oldest first.
 int surrogate_learn(game_ctx* h) {
-  const int P = h->prm.P, K = h->s.K;
+  const int P = h->prm.P, K = h->Kg;
   const int slot = h->ring_head;
   CK(cudaMemcpyAsync(h->rX[slot], h->pop[h->cur], (size_t)P * K * sizeof(float),
                      cudaMemcpyDeviceToDevice, h->st));
@@ -436,7 +488,7 @@ int surrogate_learn(game_ctx* h) {
 // Buffers of the screened generation; the surrogate warm-started on the
 // current population (20 steps).
 int setup_screening(game_ctx* h) {
-  const int P = h->prm.P, K = h->s.K, E = h->prm.elitism;
+  const int P = h->prm.P, K = h->Kg, E = h->prm.elitism;
   const int n = h->prm.oversample * (P - E);
   if (dev_alloc(&h->off, (size_t)(E + n) * K) != cudaSuccess ||
       dev_alloc(&h->oplan, (size_t)(E + n)) != cudaSuccess ||
@@ -522,13 +574,36 @@ int validate_params(const game_params& p, const Shape& s, std::string* why) {
     *why = "check_every must be >= 0";
     return 0;
   }
+  if (p.selection < GAME_SEL_TOURNAMENT || p.selection > GAME_SEL_ROULETTE) {
+    *why = "unknown selection";
+    return 0;
+  }
+  if (p.selection == GAME_SEL_RANKING && P > kMaxRankingP) {
+    *why = "ranking selection needs P <= 16384";
+    return 0;
+  }
+  if (p.tied != 0 && p.tied != 1) {
+    *why = "tied must be 0 or 1";
+    return 0;
+  }
+  if (p.error < GAME_ERR_MSE || p.error > GAME_ERR_MAE) {
+    *why = "unknown error function";
+    return 0;
+  }
+  if (p.error == GAME_ERR_MAE && (p.precision == GAME_PREC_GRAM || p.rescore_top != 0)) {
+    *why = "the MAE has no Gram form: use a direct precision and rescore_top = 0";
+    return 0;
+  }
   return 1;
 }
 
 GaDev ga_dev(const game_ctx* h) {
   GaDev g;
+  g.sel = h->prm.selection;
+  g.order = h->sel_order;
+  g.cum = h->sel_cum;
   g.P = h->prm.P;
-  g.K = h->s.K;
+  g.K = h->Kg;
   g.E = h->prm.elitism;
   g.T = h->prm.tournament;
   g.I = h->prm.immigrants;
@@ -551,6 +626,9 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->plan);
   dev_free(h->status);
   dev_free(h->cand);
+  dev_free(h->sel_order);
+  dev_free(h->sel_cum);
+  dev_free(h->rpop);
   dev_free(h->popT);
   dev_free(h->popA);
   dev_free(h->a0);
@@ -610,6 +688,9 @@ int game_params_default(game_params* out) {
   out->rescore_top = 8;
   out->surrogate = 0;
   out->oversample = 8;
+  out->selection = GAME_SEL_TOURNAMENT;
+  out->tied = 0;
+  out->error = GAME_ERR_MSE;
   return GAME_OK;
 }
 
@@ -641,10 +722,12 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   std::string why;
   if (!validate_params(p, s, &why)) return fail(GAME_EINVAL, why);
   if (p.P == 0) p.P = s.B * N + 1;   // Eq. 4
+  const int Kg = p.tied ? s.B * degree + 1 : s.K;   // Eq. 5 with shared genes
 
   game_ctx* h = new (std::nothrow) game_ctx();
   if (!h) return fail(GAME_ENOMEM, "handle allocation");
   h->s = s;
+  h->Kg = Kg;
   h->prm = p;
   h->st = static_cast<cudaStream_t>(cuda_stream);
   int rc = GAME_OK;
@@ -659,12 +742,15 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
 
   if (dev_alloc(&h->Xt, (size_t)s.Mpad * N) != cudaSuccess ||
       dev_alloc(&h->y, (size_t)s.Mpad) != cudaSuccess ||
-      dev_alloc(&h->pop[0], (size_t)p.P * s.K) != cudaSuccess ||
-      dev_alloc(&h->pop[1], (size_t)p.P * s.K) != cudaSuccess ||
+      dev_alloc(&h->pop[0], (size_t)p.P * Kg) != cudaSuccess ||
+      dev_alloc(&h->pop[1], (size_t)p.P * Kg) != cudaSuccess ||
       dev_alloc(&h->fit, (size_t)p.P) != cudaSuccess ||
       dev_alloc(&h->plan, (size_t)p.P) != cudaSuccess ||
       dev_alloc(&h->status, 4) != cudaSuccess ||
-      dev_alloc(&h->cand, kMaxRescore) != cudaSuccess) {
+      dev_alloc(&h->cand, kMaxRescore) != cudaSuccess ||
+      (p.selection == GAME_SEL_RANKING && dev_alloc(&h->sel_order, (size_t)p.P) != cudaSuccess) ||
+      (p.selection == GAME_SEL_ROULETTE &&
+       dev_alloc(&h->sel_cum, (size_t)p.P + 1) != cudaSuccess)) {
     cudaGetLastError();
     return bail(fail(GAME_ENOMEM, "device allocation of the training set / GA state"));
   }
@@ -701,7 +787,7 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   if (bad_h[1]) return bail(fail(GAME_EINVAL, "Chebyshev basis needs features in [-1, 1]"));
 
   // generation 0: uniform genes, then their fitness
-  e = launch_init_population(p.seed, p.P, s.K, h->pop[0], h->st);
+  e = launch_init_population(p.seed, p.P, Kg, h->pop[0], h->st);
   if (e != cudaSuccess) return bail(cuda_fail(e, "init population"));
   rc = eval_state(h);
   if (rc) return bail(rc);
@@ -721,7 +807,7 @@ int game_get_shape(game_t h, int64_t* M, int32_t* N, int32_t* K, int32_t* P) {
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   if (M) *M = h->s.M;
   if (N) *N = h->s.N;
-  if (K) *K = h->s.K;
+  if (K) *K = h->Kg;
   if (P) *P = h->prm.P;
   return GAME_OK;
 }
@@ -741,14 +827,14 @@ int game_eval_fitness_prec(game_t h, const float* pop, int32_t P, int32_t precis
     h->upop = nullptr;
     h->ufit = nullptr;
     h->ucap = 0;
-    if (dev_alloc(&h->upop, (size_t)P * h->s.K) != cudaSuccess ||
+    if (dev_alloc(&h->upop, (size_t)P * h->Kg) != cudaSuccess ||
         dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
       cudaGetLastError();
       return fail(GAME_ENOMEM, "device copy of the population");
     }
     h->ucap = P;
   }
-  CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->s.K * sizeof(float), cudaMemcpyHostToDevice,
+  CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->Kg * sizeof(float), cudaMemcpyHostToDevice,
                      h->st));
   int rc = eval_device(h, h->upop, P, precision, h->ufit);
   if (rc) return rc;
@@ -779,14 +865,14 @@ int game_rescore_top(game_t h, const float* pop, int32_t P, double* fit, int32_t
       h->upop = nullptr;
       h->ufit = nullptr;
       h->ucap = 0;
-      if (dev_alloc(&h->upop, (size_t)P * h->s.K) != cudaSuccess ||
+      if (dev_alloc(&h->upop, (size_t)P * h->Kg) != cudaSuccess ||
           dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
         cudaGetLastError();
         return fail(GAME_ENOMEM, "device copy of the population");
       }
       h->ucap = P;
     }
-    CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->s.K * sizeof(float),
+    CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->Kg * sizeof(float),
                        cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->ufit, fit, (size_t)P * sizeof(double), cudaMemcpyHostToDevice, h->st));
     rc = rescore_device(h, h->upop, P, n, h->ufit);
@@ -813,7 +899,7 @@ int game_generation(game_t h, uint64_t seed) {
   if (h->prm.surrogate) {
     // oversampled offspring, screened by the surrogate
     GaDev g = ga_dev(h);
-    const int E = h->prm.elitism, P = h->prm.P, K = h->s.K;
+    const int E = h->prm.elitism, P = h->prm.P, K = h->Kg;
     const int n = h->prm.oversample * (P - E);
     g.Nout = E + n;
     cudaEvent_t t0 = stage_begin(h);
@@ -897,7 +983,7 @@ int game_get_population(game_t h, float* pop_out, double* fit_out, int64_t* gene
   bool host = false;
   if (pop_out) {
     host |= !is_device_ptr(pop_out);
-    CK(cudaMemcpyAsync(pop_out, h->pop[h->cur], (size_t)h->prm.P * h->s.K * sizeof(float),
+    CK(cudaMemcpyAsync(pop_out, h->pop[h->cur], (size_t)h->prm.P * h->Kg * sizeof(float),
                        cudaMemcpyDefault, h->st));
   }
   if (fit_out) {
@@ -918,7 +1004,7 @@ int game_set_state(game_t h, const float* pop, const double* fit, int64_t genera
   g_last_error.clear();
   if (!h || !pop) return fail(GAME_EINVAL, "NULL argument");
   if (generation < 0 || generation >= 0xFFFFFFFFll) return fail(GAME_EINVAL, "bad generation");
-  int rc = copy_in(h, h->pop[h->cur], pop, (size_t)h->prm.P * h->s.K * sizeof(float));
+  int rc = copy_in(h, h->pop[h->cur], pop, (size_t)h->prm.P * h->Kg * sizeof(float));
   if (rc) return rc;
   if (fit) {
     rc = copy_in(h, h->fit, fit, (size_t)h->prm.P * sizeof(double));
@@ -974,7 +1060,7 @@ int surrogate_inputs(game_ctx* h, const float* pop, const double* fit, int n) {
     h->ufitd = nullptr;
     h->upred = nullptr;
     h->sur_cap = 0;
-    if (dev_alloc(&h->uX, (size_t)n * h->s.K) != cudaSuccess ||
+    if (dev_alloc(&h->uX, (size_t)n * h->Kg) != cudaSuccess ||
         dev_alloc(&h->ufitd, (size_t)n) != cudaSuccess ||
         dev_alloc(&h->upred, (size_t)n) != cudaSuccess) {
       cudaGetLastError();
@@ -982,7 +1068,7 @@ int surrogate_inputs(game_ctx* h, const float* pop, const double* fit, int n) {
     }
     h->sur_cap = n;
   }
-  CK(cudaMemcpyAsync(h->uX, pop, (size_t)n * h->s.K * sizeof(float), cudaMemcpyDefault, h->st));
+  CK(cudaMemcpyAsync(h->uX, pop, (size_t)n * h->Kg * sizeof(float), cudaMemcpyDefault, h->st));
   if (fit) CK(cudaMemcpyAsync(h->ufitd, fit, (size_t)n * sizeof(double), cudaMemcpyDefault, h->st));
   return ensure_surrogate(h, n);
 }
@@ -1006,7 +1092,7 @@ int game_surrogate_grad(game_t h, const float* pop, const double* fit, int32_t n
   if (rc) return rc;
   CK(surrogate_forward(h->sd, h->uX, n, h->sd.out, h->st));
   CK(surrogate_backward(h->sd, h->uX, h->ufitd, n, h->st));
-  CK(cudaMemcpyAsync(grad_out, h->sd.g, surrogate_param_count(h->s.K) * sizeof(float),
+  CK(cudaMemcpyAsync(grad_out, h->sd.g, surrogate_param_count(h->Kg) * sizeof(float),
                      cudaMemcpyDefault, h->st));
   if (loss_out) CK(cudaMemcpyAsync(loss_out, h->sd.loss, sizeof(float), cudaMemcpyDefault, h->st));
   return check_status(h);
@@ -1025,7 +1111,7 @@ int game_surrogate_train(game_t h, const float* pop, const double* fit, int32_t 
 int game_surrogate_params(game_t h, float* w_out, int64_t* count) {
   g_last_error.clear();
   if (!h || !count) return fail(GAME_EINVAL, "bad argument");
-  *count = surrogate_param_count(h->s.K);
+  *count = surrogate_param_count(h->Kg);
   if (!w_out) return GAME_OK;
   int rc = ensure_surrogate(h, 1);
   if (rc) return rc;
@@ -1038,7 +1124,7 @@ int game_surrogate_set_params(game_t h, const float* w) {
   if (!h || !w) return fail(GAME_EINVAL, "bad argument");
   int rc = ensure_surrogate(h, 1);
   if (rc) return rc;
-  const int64_t n = surrogate_param_count(h->s.K);
+  const int64_t n = surrogate_param_count(h->Kg);
   CK(cudaMemcpyAsync(h->sd.w, w, n * sizeof(float), cudaMemcpyDefault, h->st));
   CK(cudaMemsetAsync(h->sd.m, 0, n * sizeof(float), h->st));
   CK(cudaMemsetAsync(h->sd.v, 0, n * sizeof(float), h->st));
@@ -1069,7 +1155,7 @@ int game_gram(game_t h, double* G_out, double* b_out, double* yy_out) {
   if (!h) return fail(GAME_EINVAL, "NULL handle");
   int rc = ensure_gram(h);
   if (rc) return rc;
-  const int K = h->s.K;
+  const int K = h->Kg;
   if (G_out) CK(cudaMemcpyAsync(G_out, h->G, (size_t)K * K * sizeof(double), cudaMemcpyDefault, h->st));
   if (b_out) CK(cudaMemcpyAsync(b_out, h->gb, (size_t)K * sizeof(double), cudaMemcpyDefault, h->st));
   if (yy_out) CK(cudaMemcpyAsync(yy_out, h->gyy, sizeof(double), cudaMemcpyDefault, h->st));

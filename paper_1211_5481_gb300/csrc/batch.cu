@@ -551,6 +551,8 @@ int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* p
       p.immigrants < 0 || !(p.pc >= 0.f && p.pc <= 1.f) || !(p.pm >= 0.f && p.pm <= 1.f) ||
       !(p.sigma >= 0.f) || !std::isfinite(p.sigma))
     return bfail(GAME_EINVAL, "bad GA settings");
+  if (p.selection != GAME_SEL_TOURNAMENT || p.tied != 0 || p.error != GAME_ERR_MSE)
+    return bfail(GAME_EINVAL, "batched runs use tournament selection, per-feature genes and MSE");
   game_batch* b = new (std::nothrow) game_batch();
   if (!b) return bfail(GAME_ENOMEM, "batch handle");
   auto bail = [&](int code) {

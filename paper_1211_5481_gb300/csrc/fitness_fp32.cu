@@ -10,8 +10,9 @@
 // popT (coalesced), the chunk of the expansion phi is generated in registers
 // from the features (basis.cuh) and staged through shared memory, double
 // buffered. Neither phi nor the output block ever reaches global memory: the
-// epilogue forms the residuals, squares and sums them over the tile's
-// patterns (FP32, 128 terms), and adds the tile sum to an FP64 accumulator
+// epilogue forms the residuals, squares them (or, for the MAE, takes their
+// absolute values) and sums them over the tile's patterns (FP32, 128 terms),
+// and adds the tile sum to an FP64 accumulator
 // per chromosome. Each CTA writes its FP64 sums to part[blockIdx.y][p]; the
 // reduce kernel adds the rows in a fixed order.
 #include "basis.cuh"
@@ -26,6 +27,7 @@ constexpr int BM = 128;   // patterns per tile
 constexpr int KC = 16;    // contraction columns per chunk
 constexpr int kThreads = 256;
 
+template <bool ABS>
 __global__ void __launch_bounds__(kThreads, 2)
 fitness_fp32_kernel(int64_t M, int N, int d, int basis, int Kp, int Kc,
                     const float* __restrict__ Xt, const float* __restrict__ y,
@@ -123,7 +125,7 @@ fitness_fp32_kernel(int64_t M, int N, int d, int basis, int Kp, int Kc,
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         const float r = (yv[v] - bias) - acc[u][v];
-        s = ok[v] ? fmaf(r, r, s) : s;
+        s = ok[v] ? (ABS ? s + fabsf(r) : fmaf(r, r, s)) : s;
       }
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
@@ -155,12 +157,13 @@ Fp32Plan plan_fp32(const Shape& s, int P, int num_sms) {
 
 cudaError_t launch_fitness_fp32(const Fp32Plan& pl, const Shape& s, const float* Xt,
                                 const float* y, const float* popT, const float* a0, int P,
-                                int Ppad, double* part, cudaStream_t st) {
+                                int Ppad, double* part, int err, cudaStream_t st) {
   (void)P;
   const int ntiles = ceil_div(s.M, BM);
   dim3 grid(pl.grid_x, pl.grid_y);
-  fitness_fp32_kernel<<<grid, kThreads, 0, st>>>(s.M, s.N, s.d, s.basis, s.Kp, pl.Kc, Xt, y,
-                                                 popT, a0, Ppad, ntiles, part);
+  auto kern = err == GAME_ERR_MAE ? fitness_fp32_kernel<true> : fitness_fp32_kernel<false>;
+  kern<<<grid, kThreads, 0, st>>>(s.M, s.N, s.d, s.basis, s.Kp, pl.Kc, Xt, y, popT, a0, Ppad,
+                                  ntiles, part);
   return cudaGetLastError();
 }
 

@@ -237,7 +237,7 @@ int eval_fitness_static(const float* X, const float* y, int64_t M, int32_t N, in
                                                    P, (int)Ppad, ntiles, part);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GAME_ECUDA, cudaGetErrorString(e));
-  e = launch_reduce(part, (int)rows, P, (int)Ppad, M, fit_out, st);
+  e = launch_reduce(part, (int)rows, P, (int)Ppad, M, GAME_ERR_MSE, fit_out, st);
   if (e != cudaSuccess) return fail(GAME_ECUDA, cudaGetErrorString(e));
   return GAME_OK;
 }

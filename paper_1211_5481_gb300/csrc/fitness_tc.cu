@@ -107,7 +107,8 @@ __host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages,
 
 // TRI: the 192-pattern tile (three expansion rows per thread), instantiated
 // for the BF16 form only, so the 128- and 256-pattern code stays lean.
-template <int F, bool TRI>
+// ABS: the epilogue sums absolute residuals (MAE) instead of squared ones.
+template <int F, bool TRI, bool ABS>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a) {
   constexpr int NA = form_na(F), NPHI = form_nphi(F), CPK = form_cols(F) / 8;
   extern __shared__ uint8_t smem_raw[];
@@ -374,12 +375,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int k = 0; k < nfull; k += 2) {
             const bool has_b = k + 1 < nfull;
             if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
-            epi_chunk<F == kFormFP8>(va, yt + k * 32, bias2, negu2, s2);
+            epi_chunk<F == kFormFP8, ABS>(va, yt + k * 32, bias2, negu2, s2);
             if (has_b) {
               ptx::tmem_ld32_wait(vb);
               const bool has_a = k + 2 < nfull;
               if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
-              epi_chunk<F == kFormFP8>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
+              epi_chunk<F == kFormFP8, ABS>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
               if (has_a) ptx::tmem_ld32_wait(va);
             }
           }
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int e = 0; e < 32; ++e) {
             if (e < lim) {
               const float r = fmaf(negu, __uint_as_float(v[e]), yt[nfull * 32 + e] - bias);
-              s_tail = fmaf(r, r, s_tail);
+              s_tail = ABS ? s_tail + fabsf(r) : fmaf(r, r, s_tail);
             }
           }
         }
@@ -656,10 +657,21 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
   return pl;
 }
 
+template <bool ABS>
+using TcKernel = void (*)(const TcArgs);
+
+template <bool ABS>
+TcKernel<ABS> pick_kernel(const TcPlan& pl) {
+  return pl.form == kFormBF16x3 ? fitness_tc_kernel<kFormBF16x3, false, ABS>
+         : pl.form == kFormFP8  ? fitness_tc_kernel<kFormFP8, false, ABS>
+         : pl.BN == 192         ? fitness_tc_kernel<kFormBF16, true, ABS>
+                                : fitness_tc_kernel<kFormBF16, false, ABS>;
+}
+
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0,
                               const float* uscale, const float* colinv, int P, int Ppad,
-                              double* part, int* status, cudaStream_t st) {
+                              double* part, int* status, int err, cudaStream_t st) {
   (void)P;
   if (!pl.ok) return cudaErrorInvalidValue;
   TcArgs a;
@@ -688,10 +700,7 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.status = status;
   if (pl.form == kFormFP8 && (!uscale || !colinv)) return cudaErrorInvalidValue;
   if (pl.BN == 192 && pl.form != kFormBF16) return cudaErrorInvalidValue;
-  void (*kern)(const TcArgs) = pl.form == kFormBF16x3 ? fitness_tc_kernel<kFormBF16x3, false>
-                               : pl.form == kFormFP8  ? fitness_tc_kernel<kFormFP8, false>
-                               : pl.BN == 192         ? fitness_tc_kernel<kFormBF16, true>
-                                                      : fitness_tc_kernel<kFormBF16, false>;
+  void (*kern)(const TcArgs) = err == GAME_ERR_MAE ? pick_kernel<true>(pl) : pick_kernel<false>(pl);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        pl.smem_bytes);
   if (e != cudaSuccess) return e;

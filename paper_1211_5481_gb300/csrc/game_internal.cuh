@@ -47,6 +47,7 @@ struct Shape {
   int N, d, basis, B;
   int K;      // genes, B*N*d + 1
   int Kp;     // K - 1, the contraction length
+  int tied;   // Gram form only: 1 = shared genes, K = B*d + 1 over psi = sum_i phi(x_i)
 };
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
@@ -57,12 +58,18 @@ cudaError_t launch_relayout_X(const float* X, const float* y, const Shape& s, fl
                               float* yp, int* bad_counts, cudaStream_t st);
 cudaError_t launch_pack_fp32(const float* pop, int P, int Ppad, const Shape& s, int Kc,
                              float* popT, float* a0, cudaStream_t st);
+// full [P][s.K] = the shared-gene population pop [P][B*d + 1] with its genes
+// repeated for every feature: full[p][0] = pop[p][0],
+// full[p][1 + i B d + c] = pop[p][1 + c]
+cudaError_t launch_replicate_tied(const float* pop, int P, const Shape& s, float* full,
+                                  cudaStream_t st);
 // fitness_fp32.cu
 struct Fp32Plan { int BP, BM, Kc, grid_x, grid_y; };
 Fp32Plan plan_fp32(const Shape& s, int P, int num_sms);
+// err: GAME_ERR_MAE sums absolute residuals, any other value squared ones
 cudaError_t launch_fitness_fp32(const Fp32Plan& pl, const Shape& s, const float* Xt,
                                 const float* y, const float* popT, const float* a0, int P,
-                                int Ppad, double* part, cudaStream_t st);
+                                int Ppad, double* part, int err, cudaStream_t st);
 // fitness_tc.cu -- operand forms of the tensor-core contraction
 enum TcForm : int { kFormBF16 = 0, kFormBF16x3 = 1, kFormFP8 = 2 };
 // 16 KB gene blocks per (chromosome tile, K-block): hi and lo for bf16x3
@@ -73,10 +80,11 @@ __host__ __device__ constexpr int form_nphi(int f) { return f == kFormBF16x3 ? 2
 __host__ __device__ constexpr int form_cols(int f) { return f == kFormFP8 ? 128 : 64; }
 struct TcPlan { int form, BN, KB, NS, C, stages, grid, smem_bytes, tmem_cols, rows; bool ok; };
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form);
+// err: GAME_ERR_MAE sums absolute residuals, any other value squared ones
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0,
                               const float* uscale, const float* colinv, int P, int Ppad,
-                              double* part, int* status, cudaStream_t st);
+                              double* part, int* status, int err, cudaStream_t st);
 // layout.cu: FP8 column scales. colmax [KB*128] receives max_m |phi_k(x_m)|
 // as FP32 bit patterns (zero-initialised by the caller); scales turns it into
 // colscale = colmax / 448 and colinv = 448 / colmax (0 where colmax is 0).
@@ -161,21 +169,22 @@ cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, d
                               double* b, double* yy, double* phi_chunk, double* part,
                               cudaStream_t st);
 // fit of the P chromosomes pop [P][K] (idx NULL), or of rows idx[0..P-1]
-// written to fit[idx[p]]
+// written to fit[idx[p]]; err GAME_ERR_MSE or GAME_ERR_RMSE
 cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const int* idx,
                                 const double* G, const double* b, const double* yy,
-                                double* fit, cudaStream_t st);
+                                double* fit, int err, cudaStream_t st);
 // the elite re-scoring: n <= kMaxRescore chromosomes pop rows idx[q], spread
 // over the GPU; part [gram_small_parts(s) * n] is scratch
 int gram_small_parts(const Shape& s);
 cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const int* idx,
                                 const double* G, const double* b, const double* yy,
-                                double* part, double* fit, cudaStream_t st);
+                                double* part, double* fit, int err, cudaStream_t st);
 
 // api.cu
 void record_error(const char* msg);
 // reduce.cu
-cudaError_t launch_reduce(const double* part, int rows, int P, int Ppad, int64_t M,
+// fit[p] = (sum of the rows) / M, or its square root for GAME_ERR_RMSE
+cudaError_t launch_reduce(const double* part, int rows, int P, int Ppad, int64_t M, int err,
                           double* fit, cudaStream_t st);
 // ga_ops.cu
 struct GaDev {
@@ -183,7 +192,11 @@ struct GaDev {
   int Nout;   // output slots: P for a generation, more for oversampled offspring
   uint32_t thr_pc, thr_pm;
   float sigma;
+  int sel = GAME_SEL_TOURNAMENT;   // GAME_SEL_*
+  int* order = nullptr;            // ranking: chromosome of rank r [P]
+  uint64_t* cum = nullptr;         // roulette: inclusive weight sums, cum[0] = 0 [P + 1]
 };
+constexpr int kMaxRankingP = 16384;   // ranking sorts the population in shared memory
 cudaError_t launch_init_population(uint64_t seed, int P, int K, float* pop, cudaStream_t st);
 cudaError_t launch_generation(const GaDev& ga, const float* pop, const double* fit,
                               uint64_t seed, uint32_t g, int4* plan, float* next,

@@ -11,6 +11,12 @@
 // P K^2 FP64 multiply-adds instead of M P K. The subtraction cancels when the
 // fit is good (fit << yy / M), which is why everything here is FP64.
 //
+// Shared genes (Eq. 2 as printed): the expansion is
+// psi~(x) = (1, psi_1(x), ..., psi_{B d}(x)) with psi_{b,j}(x) =
+// sum_i phi_{b,j}(x_i) (features in order), written by expand_tied_kernel;
+// everything else is the same with K = B d + 1.
+// RMSE: the square root of the MSE (clamped at 0 against cancellation).
+//
 // Accumulation: the patterns are taken in chunks of up to kChunk; a chunk's
 // design matrix Phi [mc][K] (FP64) is written by expand_kernel, then
 // gram_accum_kernel adds Phi^T Phi into the upper triangle of G (64 x 64
@@ -67,6 +73,49 @@ __global__ void expand_kernel(int64_t m0, int mc, int N, int d, int basis, int K
       }
     }
   }
+}
+
+// Psi[r][c] for patterns m0 + r with shared genes: column 0 is 1, column
+// 1 + b d + (j - 1) the sum over features i = 0..N-1, in order, of
+// phi_{b,j}(x_i); K = B d + 1.
+__global__ void expand_tied_kernel(int64_t m0, int mc, int N, int d, int basis, int K,
+                                   const float* __restrict__ Xt, double* __restrict__ Phi) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < mc; r += gridDim.x * blockDim.x) {
+    const int64_t m = m0 + r;
+    double* row = Phi + (int64_t)r * K;
+    row[0] = 1.0;
+    for (int c = 1; c < K; ++c) row[c] = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double x = (double)Xt[(m / kPatBlock) * (int64_t)N * kPatBlock +
+                                  (int64_t)i * kPatBlock + m % kPatBlock];
+      if (basis == GAME_BASIS_CHEB) {
+        double tm = 1.0, t = x;
+        for (int j = 1; j <= d; ++j) {
+          row[j] += t;
+          const double tn = 2.0 * x * t - tm;
+          tm = t;
+          t = tn;
+        }
+      } else {
+        double s1, c1;
+        sincos(x, &s1, &c1);
+        for (int bb = 0; bb < 2; ++bb) {
+          double fm = bb ? 0.0 : 1.0, f = bb ? s1 : c1;
+          for (int j = 1; j <= d; ++j) {
+            row[1 + bb * d + j - 1] += f;
+            const double fn = 2.0 * c1 * f - fm;
+            fm = f;
+            f = fn;
+          }
+        }
+      }
+    }
+  }
+}
+
+// The fitness from the MSE: itself, or its square root for GAME_ERR_RMSE.
+__device__ __forceinline__ double finish_error(double mse, int err) {
+  return err == GAME_ERR_RMSE ? sqrt(fmax(mse, 0.0)) : mse;
 }
 
 // part[z][k1][k2] = sum over rows r of split z of Phi[r][k1] Phi[r][k2], for
@@ -165,7 +214,7 @@ __global__ void mirror_kernel(int K, double* __restrict__ G) {
 // with idx, entry p is chromosome idx[p] (read from pop row idx[p], written to
 // fit[idx[p]]).
 __global__ void __launch_bounds__(256)
-quad_kernel(int P, int K, int64_t M, int grp, const float* __restrict__ pop,
+quad_kernel(int P, int K, int64_t M, int grp, int err, const float* __restrict__ pop,
             const int* __restrict__ idx, const double* __restrict__ G,
             const double* __restrict__ b, const double* __restrict__ yy,
             double* __restrict__ fit) {
@@ -217,7 +266,7 @@ quad_kernel(int P, int K, int64_t M, int grp, const float* __restrict__ pop,
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
     const int p = p0 + threadIdx.x;
-    fit[idx ? idx[p] : p] = (*yy + s) / (double)M;
+    fit[idx ? idx[p] : p] = finish_error((*yy + s) / (double)M, err);
   }
 }
 
@@ -277,14 +326,15 @@ quad_small_kernel(int n, int K, int ks, const float* __restrict__ pop, const int
   }
 }
 
-__global__ void quad_small_finish(int n, int nparts, int64_t M, const int* __restrict__ idx,
+__global__ void quad_small_finish(int n, int nparts, int64_t M, int err,
+                                  const int* __restrict__ idx,
                                   const double* __restrict__ part, const double* __restrict__ yy,
                                   double* __restrict__ fit) {
   const int q = threadIdx.x;
   if (q >= n) return;
   double s = 0.0;
   for (int j = 0; j < nparts; ++j) s += part[(int64_t)j * n + q];
-  fit[idx[q]] = (*yy + s) / (double)M;
+  fit[idx[q]] = finish_error((*yy + s) / (double)M, err);
 }
 
 int blocks_for(int64_t n) {
@@ -316,8 +366,12 @@ cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, d
   const int KT = (K + kGT - 1) / kGT;
   for (int64_t m0 = 0; m0 < s.M; m0 += CH) {
     const int mc = (int)(s.M - m0 < CH ? s.M - m0 : CH);
-    expand_kernel<<<blocks_for((int64_t)mc * s.N), 256, 0, st>>>(m0, mc, s.N, s.d, s.basis, K,
-                                                                Xt, phi_chunk);
+    if (s.tied)
+      expand_tied_kernel<<<blocks_for(mc), 256, 0, st>>>(m0, mc, s.N, s.d, s.basis, K, Xt,
+                                                         phi_chunk);
+    else
+      expand_kernel<<<blocks_for((int64_t)mc * s.N), 256, 0, st>>>(m0, mc, s.N, s.d, s.basis,
+                                                                  K, Xt, phi_chunk);
     const int rs = (mc + kGramSplits - 1) / kGramSplits;
     gram_accum_kernel<<<dim3(KT, KT, kGramSplits), 256, 0, st>>>(mc, rs, K, phi_chunk, part);
     gram_add_kernel<<<blocks_for((int64_t)K * K), 256, 0, st>>>(K, kGramSplits, part, G);
@@ -338,7 +392,7 @@ int gram_small_parts(const Shape& s) {
 
 cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const int* idx,
                                 const double* G, const double* b, const double* yy,
-                                double* part, double* fit, cudaStream_t st) {
+                                double* part, double* fit, int err, cudaStream_t st) {
   if (n < 1 || n > kMaxRescore) return cudaErrorInvalidValue;
   const int bx = (s.K + kSmallRows - 1) / kSmallRows;
   const int by = gram_small_parts(s) / bx;
@@ -352,13 +406,13 @@ cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const i
   quad_small_kernel<<<dim3(bx, by), kSmallRows, smem, st>>>(n, s.K, ks, pop, idx, G, b, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  quad_small_finish<<<1, 32, 0, st>>>(n, bx * by, s.M, idx, part, yy, fit);
+  quad_small_finish<<<1, 32, 0, st>>>(n, bx * by, s.M, err, idx, part, yy, fit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const int* idx,
                                 const double* G, const double* b, const double* yy,
-                                double* fit, cudaStream_t st) {
+                                double* fit, int err, cudaStream_t st) {
   // as many chromosomes per CTA (<= 8) as fit in 200 KB of FP64 genes
   int grp = (int)((200 * 1024) / ((size_t)s.K * sizeof(double)));
   if (grp > kQuadGroup) grp = kQuadGroup;
@@ -367,8 +421,8 @@ cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const i
   cudaError_t e = cudaFuncSetAttribute(quad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024);
   if (e != cudaSuccess) return e;
-  quad_kernel<<<(P + grp - 1) / grp, 256, smem, st>>>(P, s.K, s.M, grp, pop, idx, G, b, yy,
-                                                       fit);
+  quad_kernel<<<(P + grp - 1) / grp, 256, smem, st>>>(P, s.K, s.M, grp, err, pop, idx, G, b,
+                                                       yy, fit);
   return cudaGetLastError();
 }
 

@@ -222,6 +222,20 @@ __global__ void colscales_kernel(const unsigned int* __restrict__ colmax, int nc
   }
 }
 
+// full[p][k] = pop[p][0] for k = 0, else pop[p][1 + (k - 1) mod (B d)]:
+// gene 1 + i B d + b d + (j - 1) of feature i takes the shared gene
+// 1 + b d + (j - 1).
+__global__ void replicate_tied_kernel(const float* __restrict__ pop, int P, int K, int Bd,
+                                      float* __restrict__ full) {
+  const int64_t n = (int64_t)P * K;
+  const int Kg = Bd + 1;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / K), k = (int)(e % K);
+    full[e] = pop[(int64_t)p * Kg + (k == 0 ? 0 : 1 + (k - 1) % Bd)];
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return (int)(b < 65535 * 16 ? (b < 1 ? 1 : b) : 65535 * 16);
@@ -241,6 +255,13 @@ cudaError_t launch_pack_fp32(const float* pop, int P, int Ppad, const Shape& s, 
                              float* popT, float* a0, cudaStream_t st) {
   const int64_t n = (int64_t)Kc * Ppad;
   pack_fp32_kernel<<<grid_for(n, 256), 256, 0, st>>>(pop, P, Ppad, s.K, Kc, popT, a0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replicate_tied(const float* pop, int P, const Shape& s, float* full,
+                                  cudaStream_t st) {
+  const int64_t n = (int64_t)P * s.K;
+  replicate_tied_kernel<<<grid_for(n, 256), 256, 0, st>>>(pop, P, s.K, s.B * s.d, full);
   return cudaGetLastError();
 }
 

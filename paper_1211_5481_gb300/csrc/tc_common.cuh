@@ -1,6 +1,7 @@
 // tc_common.cuh -- device helpers shared by the tensor-core fitness kernels
 // (single problem and batched): bounded mbarrier waits, the fused
-// squared-error epilogue step, and operand rounding to BF16 / E4M3.
+// squared- or absolute-error epilogue step, and operand rounding to BF16 /
+// E4M3.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -45,11 +46,12 @@ static __device__ void wait_bar_drain(uint32_t bar, uint32_t parity, int* status
   }
 }
 
-// sse += ((y - bias) - u * acc)^2 over 32 columns, two columns per packed op.
+// sse += ((y - bias) - u * acc)^2 over 32 columns, two columns per packed op
+// (ABS: += |(y - bias) - u * acc|, the absolute error).
 // SCALED = false: u = 1 and the residual is one packed subtraction; true
 // (FP8): -u * acc + (y - bias) as one packed FMA (one rounding, as the
 // subtraction is for u = 1).
-template <bool SCALED>
+template <bool SCALED, bool ABS = false>
 __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* yc,
                                           uint64_t bias2, uint64_t negu2, uint64_t& s2) {
 #pragma unroll
@@ -61,8 +63,13 @@ __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* 
     const uint64_t db = ptx::f2_pack(__uint_as_float(v[4 * e4 + 2]), __uint_as_float(v[4 * e4 + 3]));
     const uint64_t ra = SCALED ? ptx::f2_fma(negu2, da, ya) : ptx::f2_sub(ya, da);
     const uint64_t rb = SCALED ? ptx::f2_fma(negu2, db, yb) : ptx::f2_sub(yb, db);
-    s2 = ptx::f2_fma(ra, ra, s2);
-    s2 = ptx::f2_fma(rb, rb, s2);
+    if (ABS) {
+      s2 = ptx::f2_add(s2, ptx::f2_abs(ra));
+      s2 = ptx::f2_add(s2, ptx::f2_abs(rb));
+    } else {
+      s2 = ptx::f2_fma(ra, ra, s2);
+      s2 = ptx::f2_fma(rb, rb, s2);
+    }
   }
 }
 

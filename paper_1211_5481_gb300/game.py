@@ -29,6 +29,12 @@ GAME_PREC_BF16 = 1
 GAME_PREC_BF16X3 = 2
 GAME_PREC_FP8 = 3
 GAME_PREC_GRAM = 4
+GAME_ERR_MSE = 0
+GAME_ERR_RMSE = 1
+GAME_ERR_MAE = 2
+GAME_SEL_TOURNAMENT = 0
+GAME_SEL_RANKING = 1
+GAME_SEL_ROULETTE = 2
 
 _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
               GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}
@@ -68,7 +74,10 @@ class game_params(ctypes.Structure):
         ("rescore_top", ctypes.c_int32),
         ("surrogate", ctypes.c_int32),
         ("oversample", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("selection", ctypes.c_int32),
+        ("tied", ctypes.c_int32),
+        ("error", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

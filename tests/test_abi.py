@@ -64,4 +64,42 @@ def test_host_side_argument_checks():
     rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
                          ctypes.byref(h))
     assert rc == game.GAME_EINVAL
+    assert p.selection == game.GAME_SEL_TOURNAMENT and p.tied == 0
+    assert p.error == game.GAME_ERR_MSE
+    # selection, shared genes and error function settings
+    for field, value, extra in [("selection", 3, {}), ("selection", -1, {}),
+                                ("selection", game.GAME_SEL_RANKING, {"P": 16385}),
+                                ("tied", 2, {}), ("error", 3, {}),
+                                ("error", game.GAME_ERR_MAE, {}),   # rescore_top = 8
+                                ("error", game.GAME_ERR_MAE,
+                                 {"rescore_top": 0, "precision": game.GAME_PREC_GRAM})]:
+        bad = game.game_params_default()
+        setattr(bad, field, value)
+        for k, v in extra.items():
+            setattr(bad, k, v)
+        rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
+                             ctypes.byref(h))
+        assert rc == game.GAME_EINVAL, (field, value, extra)
+    bad = game.game_params_default()
+    bad.reserved[1] = 1
+    rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
+                         ctypes.byref(h))
+    assert rc == game.GAME_EINVAL
     assert lib.game_destroy(None) == game.GAME_OK
+
+
+def test_batch_refuses_paper_mode_settings():
+    """Batched runs take tournament selection, per-feature genes and the MSE
+    only; the check precedes any device work."""
+    lib = game.load()
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.zeros(4, dtype=np.float32)
+    runs = (game.game_run_desc * 1)()
+    runs[0] = game.game_run_desc(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, 8, 1)
+    b = ctypes.c_void_p()
+    for field, value in [("selection", game.GAME_SEL_RANKING), ("tied", 1),
+                         ("error", game.GAME_ERR_RMSE)]:
+        prm = game.game_params_default()
+        setattr(prm, field, value)
+        rc = lib.game_batch_create(runs, 1, ctypes.byref(prm), None, 1, None, ctypes.byref(b))
+        assert rc == game.GAME_EINVAL, field

@@ -85,6 +85,8 @@ def _load():
         lib.oracle_fitness_err.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, i32, vp]
         lib.oracle_fitness_tied.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp]
         lib.oracle_gram.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
+        lib.oracle_predict.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+        lib.oracle_classify.argtypes = [vp, vp, i64, i32, i32, i32, vp, d, vp]
         lib.oracle_fitness_gram.argtypes = [vp, vp, d, i64, i32, vp, i32, vp]
         lib.oracle_philox4x32_10.restype = None
         lib.oracle_philox4x32_10.argtypes = [vp, vp, vp]
@@ -165,6 +167,37 @@ def fitness_tied(X, y, pop, d, basis):
     _check(_load().oracle_fitness_tied(_ptr(X), _ptr(y), M, N, d, basis, _ptr(pop),
                                        pop.shape[0], _ptr(fit)), "fitness_tied")
     return fit
+
+
+def predict(X, a, d, basis):
+    """Outputs Out(m) of one chromosome a[K] (Eq. 2) on the patterns X."""
+    X, a = _f64(X), _f64(np.ravel(a))
+    M, N = X.shape
+    assert a.shape[0] == num_genes(N, d, basis), "chromosome length"
+    out = np.zeros(M, dtype=np.float64)
+    _check(_load().oracle_predict(_ptr(X), M, N, d, basis, _ptr(a), _ptr(out)), "predict")
+    return out
+
+
+def classify(X, y, a, d, basis, threshold=0.0):
+    """(TP, FP, TN, FN): positive when y > threshold, predicted positive
+    when Out > threshold."""
+    X, y, a = _f64(X), _f64(y), _f64(np.ravel(a))
+    M, N = X.shape
+    assert a.shape[0] == num_genes(N, d, basis), "chromosome length"
+    counts = np.zeros(4, dtype=np.int64)
+    _check(_load().oracle_classify(_ptr(X), _ptr(y), M, N, d, basis, _ptr(a), float(threshold),
+                                   _ptr(counts)), "classify")
+    return tuple(int(c) for c in counts)
+
+
+def classification_metrics(counts):
+    """accuracy = (TP + TN) / M, completeness = TP / (TP + FN),
+    contamination = FP / (TP + FP) (0 for an empty denominator)."""
+    tp, fp, tn, fn = counts
+    M = tp + fp + tn + fn
+    return ((tp + tn) / M if M else 0.0, tp / (tp + fn) if tp + fn else 0.0,
+            fp / (tp + fp) if tp + fp else 0.0)
 
 
 def gram(X, y, d, basis):

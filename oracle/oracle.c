@@ -137,6 +137,29 @@ int oracle_fitness_err(const double* X, const double* y, int64_t M, int32_t N,
   return 0;
 }
 
+int oracle_predict(const double* X, int64_t M, int32_t N, int32_t d, int32_t basis,
+                   const double* a, double* out) {
+  if (M < 0 || N < 1 || d < 1 || !valid_basis(basis) || !a || !out) return -1;
+  for (int64_t m = 0; m < M; ++m) out[m] = oracle_output(a, X + m * N, N, d, basis);
+  return 0;
+}
+
+int oracle_classify(const double* X, const double* y, int64_t M, int32_t N,
+                    int32_t d, int32_t basis, const double* a, double threshold,
+                    int64_t* counts) {
+  if (M < 0 || N < 1 || d < 1 || !valid_basis(basis) || !a || !counts) return -1;
+  counts[0] = counts[1] = counts[2] = counts[3] = 0;
+  for (int64_t m = 0; m < M; ++m) {
+    const int actual = y[m] > threshold;
+    const int predicted = oracle_output(a, X + m * N, N, d, basis) > threshold;
+    if (predicted && actual) counts[0] += 1;        /* true positive */
+    else if (predicted) counts[1] += 1;             /* false positive */
+    else if (!actual) counts[2] += 1;               /* true negative */
+    else counts[3] += 1;                            /* false negative */
+  }
+  return 0;
+}
+
 int oracle_fitness(const double* X, const double* y, int64_t M, int32_t N,
                    int32_t d, int32_t basis, const double* pop, int32_t P,
                    double* fit) {

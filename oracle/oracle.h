@@ -63,6 +63,18 @@ int oracle_fitness_tied(const double* X, const double* y, int64_t M, int32_t N,
                         int32_t d, int32_t basis, const double* pop, int32_t P,
                         double* fit);
 
+/* Outputs of one chromosome a[K] (Eq. 2) on M patterns X[M][N]: out[M]. */
+int oracle_predict(const double* X, int64_t M, int32_t N, int32_t d, int32_t basis,
+                   const double* a, double* out);
+
+/* Binary classification counts of one chromosome (Section 5 reports
+ * accuracy, completeness and contamination without defining them): a
+ * pattern is a positive when y_m > threshold and is predicted positive when
+ * Out(m) > threshold. counts[4] = {TP, FP, TN, FN}. */
+int oracle_classify(const double* X, const double* y, int64_t M, int32_t N,
+                    int32_t d, int32_t basis, const double* a, double threshold,
+                    int64_t* counts);
+
 /* Gram form of the MSE: with phi~(x) = (1, phi_1(x), ..., phi_{K-1}(x)),
  * G = sum_m phi~ phi~^T [K][K], b = sum_m y_m phi~ [K], yy = sum_m y_m^2,
  * SSE_p = yy - 2 a_p^T b + a_p^T G a_p. */

@@ -180,3 +180,50 @@ def test_invalid_arguments(orc):
     with pytest.raises(ValueError):
         orc.basis_values(5, 3, 0.1)
     assert orc.num_genes(0, 3, CHEB) == -1
+
+
+def test_predict_matches_numpy_design_matrix(orc):
+    for basis, d in [(CHEB, 5), (TRIG, 3)]:
+        pr = dg.regression(21 + basis, 400, 5, 3, 0.1, degree=d, basis=basis)
+        a = dg.random_population(4, 1, pr.K)[0]
+        out = orc.predict(pr.X, a, d, basis)
+        ref = design_matrix_numpy(pr.X, d, basis) @ a.astype(np.float64)
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_classify_hand_example(orc):
+    """Degree 1, one feature, a = (0, 1): Out = x. Positives by target:
+    patterns 0, 1; predicted positive: patterns 1, 2."""
+    X = np.array([[-0.5], [0.2], [0.7], [-0.1]])
+    y = np.array([1.0, 1.0, -1.0, -1.0])
+    counts = orc.classify(X, y, np.array([0.0, 1.0]), 1, CHEB, 0.0)
+    assert counts == (1, 1, 1, 1)
+    assert orc.classification_metrics(counts) == (0.5, 0.5, 0.5)
+    # a threshold beyond every target and output: all negatives / all positives
+    assert orc.classify(X, y, np.array([0.0, 1.0]), 1, CHEB, 10.0) == (0, 0, 4, 0)
+    assert orc.classify(X, y, np.array([0.0, 1.0]), 1, CHEB, -10.0) == (4, 0, 0, 0)
+    # Out = 0.3 - x: predicted positive for x < 0.3 (patterns 0, 1, 3)
+    assert orc.classify(X, y, np.array([0.3, -1.0]), 1, CHEB, 0.0) == (2, 1, 1, 0)
+
+
+def test_classify_counts_brute_force(orc):
+    pr = dg.regression(5, 700, 4, 3, 0.2, degree=3)
+    a = dg.random_population(9, 1, pr.K, scale=0.3)[0]
+    out = design_matrix_numpy(pr.X, 3, CHEB) @ a.astype(np.float64)
+    thr = float(np.median(pr.y))
+    assert np.min(np.abs(out - thr)) > 1e-9      # no decision at the rounding level
+    act, pred = pr.y > thr, out > thr
+    ref = (int(np.sum(pred & act)), int(np.sum(pred & ~act)), int(np.sum(~pred & ~act)),
+           int(np.sum(~pred & act)))
+    assert orc.classify(pr.X, pr.y, a, 3, CHEB, thr) == ref
+
+
+def test_generating_chromosome_misclassifies_only_flipped_labels(orc):
+    """The large classification set labels sign(target) with 5% flips: its
+    generating chromosome predicts every unflipped label."""
+    pr = dg.large_classification(M=5000)
+    t = design_matrix_numpy(pr.X, 8, CHEB) @ pr.coef.astype(np.float64)
+    flipped = int(np.sum(np.where(t >= 0, 1.0, -1.0) != pr.y))
+    tp, fp, tn, fn = orc.classify(pr.X, pr.y, pr.coef, 8, CHEB, 0.0)
+    assert tp + fp + tn + fn == 5000
+    assert fp + fn == flipped and 150 < flipped < 350

@@ -86,6 +86,8 @@ def _load():
         lib.oracle_fitness_tied.argtypes = [vp, vp, i64, i32, i32, i32, vp, i32, vp]
         lib.oracle_gram.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, vp]
         lib.oracle_predict.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+        lib.oracle_train_tied.argtypes = [vp, vp, i64, i32, i32, i32, i32, vp, u64, i32, vp, vp,
+                                          vp]
         lib.oracle_classify.argtypes = [vp, vp, i64, i32, i32, i32, vp, d, vp]
         lib.oracle_fitness_gram.argtypes = [vp, vp, d, i64, i32, vp, i32, vp]
         lib.oracle_philox4x32_10.restype = None
@@ -295,4 +297,18 @@ def train(X, y, d, basis, P, G, seed, prm=None, use_gram=False):
     _check(_load().oracle_train(_ptr(X), _ptr(y), M, N, d, basis, P, ctypes.byref(prm),
                                 seed, G, int(use_gram), _ptr(pop), _ptr(fit),
                                 _ptr(best)), "train")
+    return pop, fit, best
+
+
+def train_tied(X, y, d, basis, P, G, seed, prm=None):
+    """Whole GA run on shared-gene chromosomes (K = B*d + 1)."""
+    prm = prm or ga_params()
+    X, y = _f64(X), _f64(y)
+    M, N = X.shape
+    K = num_genes_tied(d, basis)
+    pop = np.zeros((P, K), dtype=np.float32)
+    fit = np.zeros(P, dtype=np.float64)
+    best = np.zeros(G + 1, dtype=np.float64)
+    _check(_load().oracle_train_tied(_ptr(X), _ptr(y), M, N, d, basis, P, ctypes.byref(prm),
+                                     seed, G, _ptr(pop), _ptr(fit), _ptr(best)), "train_tied")
     return pop, fit, best

@@ -522,12 +522,15 @@ int oracle_rescore(const double* X, const double* y, int64_t M, int32_t N,
   return rc;
 }
 
-int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
-                 int32_t d, int32_t basis, int32_t P,
-                 const oracle_ga_params* prm, uint64_t seed, int32_t G,
-                 int32_t use_gram, float* pop, double* fit, double* best) {
-  const int64_t K = oracle_num_genes(N, d, basis);
-  if (K < 1 || M < 1 || G < 0 || !prm || P < prm->elitism + prm->immigrants + 2)
+/* The GA run behind oracle_train (tied = 0) and oracle_train_tied (1). */
+static int train_run(const double* X, const double* y, int64_t M, int32_t N,
+                     int32_t d, int32_t basis, int32_t P,
+                     const oracle_ga_params* prm, uint64_t seed, int32_t G,
+                     int32_t use_gram, int32_t tied, float* pop, double* fit,
+                     double* best) {
+  const int64_t K = tied ? oracle_num_genes_tied(d, basis) : oracle_num_genes(N, d, basis);
+  if (K < 1 || M < 1 || G < 0 || !prm || P < prm->elitism + prm->immigrants + 2 ||
+      (tied && use_gram))
     return -1;
   double* Gm = NULL;
   double* bv = NULL;
@@ -550,6 +553,7 @@ int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
     for (int64_t i = 0; i < P * K; ++i) popd[i] = (double)pop[i];
     if (!rc)
       rc = use_gram ? oracle_fitness_gram(Gm, bv, yy, M, (int32_t)K, popd, P, fit)
+           : tied   ? oracle_fitness_tied(X, y, M, N, d, basis, popd, P, fit)
                     : oracle_fitness(X, y, M, N, d, basis, popd, P, fit);
     double bf = INFINITY;
     for (int32_t p = 0; p < P; ++p)
@@ -561,6 +565,20 @@ int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
   free(Gm);
   free(bv);
   return rc;
+}
+
+int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
+                 int32_t d, int32_t basis, int32_t P,
+                 const oracle_ga_params* prm, uint64_t seed, int32_t G,
+                 int32_t use_gram, float* pop, double* fit, double* best) {
+  return train_run(X, y, M, N, d, basis, P, prm, seed, G, use_gram, 0, pop, fit, best);
+}
+
+int oracle_train_tied(const double* X, const double* y, int64_t M, int32_t N,
+                      int32_t d, int32_t basis, int32_t P,
+                      const oracle_ga_params* prm, uint64_t seed, int32_t G,
+                      float* pop, double* fit, double* best) {
+  return train_run(X, y, M, N, d, basis, P, prm, seed, G, 0, 1, pop, fit, best);
 }
 
 int oracle_set_threads(int32_t n) {

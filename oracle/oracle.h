@@ -148,6 +148,13 @@ int oracle_train(const double* X, const double* y, int64_t M, int32_t N,
                  const oracle_ga_params* prm, uint64_t seed, int32_t G,
                  int32_t use_gram, float* pop, double* fit, double* best);
 
+/* The same run on shared-gene chromosomes (Eq. 5, K = B*d + 1), the
+ * fitness by the direct form of oracle_fitness_tied. pop[P][B*d + 1]. */
+int oracle_train_tied(const double* X, const double* y, int64_t M, int32_t N,
+                      int32_t d, int32_t basis, int32_t P,
+                      const oracle_ga_params* prm, uint64_t seed, int32_t G,
+                      float* pop, double* fit, double* best);
+
 /* Threads the OpenMP loops may use (0 = runtime default); returns the count
  * in effect. */
 int oracle_set_threads(int32_t n);

@@ -332,3 +332,23 @@ def test_selection_rejects_bad_mode(orc):
     pop = orc.init_population(1, 4, 5)
     with pytest.raises(ValueError):
         orc.generation(pop, np.zeros(4), 1, 0, orc.ga_params(elitism=0, selection=3))
+
+
+def test_train_tied_with_one_feature_is_the_per_feature_run(orc):
+    """With N = 1 the shared-gene chromosome is the per-feature one: both
+    runs are identical, bit for bit."""
+    pr = dg.regression(4, 300, 1, 3, 0.05, degree=4)
+    prm = orc.ga_params(selection=orc.SEL_RANKING)
+    a = orc.train(pr.X, pr.y, 4, CHEB, 20, 15, 7, prm)
+    b = orc.train_tied(pr.X, pr.y, 4, CHEB, 20, 15, 7, prm)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_train_tied_elitist_and_shared_genes(orc):
+    pr = dg.regression(6, 500, 5, 2, 0.05, degree=3, basis=1)
+    pop, fit, best = orc.train_tied(pr.X, pr.y, 3, 1, 11, 30, 2,
+                                    orc.ga_params(selection=orc.SEL_ROULETTE))
+    assert pop.shape == (11, 7)
+    assert np.all(np.diff(best) <= 0)
+    np.testing.assert_allclose(fit, orc.fitness_tied(pr.X, pr.y, pop, 3, 1), rtol=1e-14)

@@ -45,11 +45,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--M", type=int, default=1_000_000, help="patterns (smaller for profiling)")
     ap.add_argument("--form", choices=["bf16", "bf16x3", "fp8", "fp32", "gram"], default="bf16")
-    ap.add_argument("--workload", choices=["classification", "batched", "surrogate"],
+    ap.add_argument("--workload", choices=["classification", "batched", "surrogate", "paper"],
                     default="classification",
                     help="batched: 256 independent runs of uneven shape, one graph per "
                          "generation; surrogate: the 4M-pattern regression set with "
-                         "surrogate-screened offspring, against the plain FP32 form")
+                         "surrogate-screened offspring, against the plain FP32 form; paper: "
+                         "the degree x iterations grid of Section 5 in the paper-literal "
+                         "mode on a set of the paper's data shape")
+    ap.add_argument("--selection", choices=["ranking", "roulette"], default="ranking",
+                    help="paper workload: parent selection (Section 5 names both)")
     ap.add_argument("--oracle-run", type=int, default=0, metavar="G",
                     help="surrogate workload: also run G generations of the FP64 oracle GA "
                          "(Gram form) and of the screened GPU GA and compare the best fitness")
@@ -58,6 +62,10 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--precision-report", type=int, default=4, metavar="G",
                     help="generations of the per-form accuracy report (0 = off)")
+    ap.add_argument("--classify-run", type=int, default=200, metavar="G",
+                    help="classification workload: after the timed steps, G more generations, "
+                         "then accuracy / completeness / contamination of the best chromosome "
+                         "(0 = off)")
     return ap.parse_args()
 
 
@@ -398,6 +406,99 @@ def run_surrogate(args, torch, game, dev, world, rank):
         print(json.dumps(line))
 
 
+PAPER_DEGREES = (1, 2, 4, 8)
+PAPER_ITERATIONS = (1000, 2000, 4000, 10000, 20000, 40000)
+
+
+def run_paper(args, torch, game, dev, world, rank):
+    """Section 5's grid, degree {1, 2, 4, 8} x iterations {1000 .. 40000},
+    with the paper's settings: trigonometric basis, shared genes (Eq. 5),
+    P = B N + 1 (Eq. 4), crossover 0.9, mutation 0.2, 2 elites, ranking or
+    roulette selection, MSE stop threshold 0.001; on a synthetic set of the
+    experiment's shape (2100 patterns, 9 features, +-1 classes). Fitness in
+    the Gram form (FP64; K = 2 d + 1). Each cell is one game_train call from
+    a fresh handle, timed on the host around the synchronous call; the FP64
+    oracle runs a bounded number of generations of the same GA per degree
+    on the host cores."""
+    from paper_1211_5481_gb300 import datagen as dg
+    pr = dg.small_classification()
+    sel = {"ranking": game.GAME_SEL_RANKING, "roulette": game.GAME_SEL_ROULETTE}[args.selection]
+    prm = dict(P=0, tied=1, elitism=2, pc=0.9, pm=0.2, selection=sel,
+               precision=game.GAME_PREC_GRAM, mse_threshold=0.001, check_every=100, seed=11)
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    for d in PAPER_DEGREES:   # warm-up: module load, first launches
+        with game.Game(Xd, yd, d, game.GAME_BASIS_TRIG, **prm) as g:
+            g.train(max(args.warmup, 3) * 10)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
+    grid = []
+    total_gen, total_s = 0, 0.0
+    for d in PAPER_DEGREES:
+        for it in PAPER_ITERATIONS:
+            with game.Game(Xd, yd, d, game.GAME_BASIS_TRIG, **prm) as g:
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                ran = g.train(it)
+                t = time.perf_counter() - t0
+                pop, fit, gen = g.population()
+                best = int(np.argmin(fit))
+                cls = g.classify(pop[best])
+            grid.append({"degree": d, "iterations": it, "generations_run": int(ran),
+                         "seconds": t, "best_mse": float(fit[best]),
+                         "accuracy": cls["accuracy"], "completeness": cls["completeness"],
+                         "contamination": cls["contamination"]})
+            total_gen += int(ran)
+            total_s += t
+    clk = clocks.stop()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = oracle.set_threads(0)
+        G_s = 400
+        per_degree = []
+        t_all = 0.0
+        for d in PAPER_DEGREES:
+            t0 = time.perf_counter()
+            oracle.train_tied(pr.X, pr.y, d, game.GAME_BASIS_TRIG, 2 * pr.N + 1, G_s, 11,
+                              oracle.ga_params(elitism=2, pc=0.9, pm=0.2, selection=sel))
+            t = time.perf_counter() - t0
+            t_all += t
+            gpu = [c for c in grid if c["degree"] == d]
+            gpu_rate = sum(c["generations_run"] for c in gpu) / sum(c["seconds"] for c in gpu)
+            per_degree.append({"degree": d, "oracle_generations_per_s": G_s / t,
+                               "gpu_generations_per_s": gpu_rate,
+                               "speedup": gpu_rate * t / G_s})
+        cpu = {"value": len(PAPER_DEGREES) * G_s / t_all, "unit": "generations/s",
+               "cores": cores, "kind": "oracle",
+               "sample": f"{G_s} generations per degree of the same GA (FP64, direct "
+                         f"shared-gene fitness)", "per_degree": per_degree}
+    line = {
+        "metric": "GAME generations/s, Section 5 degree x iterations grid (paper-literal mode)",
+        "value": total_gen * world / total_s, "unit": "generations/s", "n_gpus": world,
+        "steps": len(grid), "warmup": max(args.warmup, 3),
+        "ms_per_step": total_s / total_gen * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": pr.name, "M": pr.M, "N": pr.N, "basis": "trigonometric",
+                   "genes": "shared (Eq. 5), K = 2 d + 1", "P": 2 * pr.N + 1,
+                   "selection": args.selection, "pc": 0.9, "pm": 0.2, "elitism": 2,
+                   "stop": "MSE < 0.001, checked every 100 generations",
+                   "fitness": "Gram form, FP64",
+                   "step": "one generation (ms_per_step is the grid's mean)",
+                   "timing": "host clock around each synchronous game_train call",
+                   "l2": "inputs of 76 KB stay L2-resident (a latency-bound workload)"},
+        "grid": grid,
+        "roofline": None,
+        "roofline_note": "launch-latency bound: 19 chromosomes x 2100 patterns per generation",
+        "cpu_baseline": cpu,
+        "gpu_launches": 4 * total_gen,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -415,10 +516,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    if args.workload in ("batched", "surrogate"):
+    if args.workload in ("batched", "surrogate", "paper"):
         game.load()
-        (run_batched if args.workload == "batched" else run_surrogate)(args, torch, game, dev,
-                                                                        world, rank)
+        {"batched": run_batched, "surrogate": run_surrogate,
+         "paper": run_paper}[args.workload](args, torch, game, dev, world, rank)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -564,6 +665,23 @@ def main():
 
     n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
         2 * tm["operators_launches"] + 2 * tm["rescore_launches"]
+    cls = None
+    if rank == 0 and args.classify_run > 0:
+        # trained model quality (outside the timed region): the best
+        # chromosome after G more generations, classified by Out > 0 (labels
+        # are +-1), beside the generating polynomial's own score (the 5%
+        # flipped labels bound every model)
+        g.train(args.classify_run)
+        pop_np, fit_np, gen = g.population()
+        best = int(np.argmin(fit_np))
+        res = g.classify(pop_np[best])
+        gen_res = g.classify(pr.coef)
+        cls = {"generations": int(gen), "best_fitness": float(fit_np[best]),
+               "accuracy": res["accuracy"], "completeness": res["completeness"],
+               "contamination": res["contamination"],
+               "generating_polynomial": {k: gen_res[k] for k in
+                                         ("accuracy", "completeness", "contamination")},
+               "definition": "positive: label > 0, predicted positive: Out > 0 (FP64)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
@@ -584,6 +702,7 @@ def main():
                               for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms",
                                         "rescore_ms")},
         "accuracy": acc,
+        "classification": cls,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -214,6 +214,17 @@ int game_get_population(game_t h, float* pop_out, double* fit_out,
 int game_set_state(game_t h, const float* pop, const double* fit,
                    int64_t generation);
 
+/* Checkpoint file of the GA state: population, fitness and generation and,
+ * with the surrogate, its parameters, Adam moments and step, the judge's
+ * verdict and the replay ring, so that game_load followed by the same calls
+ * continues the run exactly. The file records M, N, degree, basis, tied, K,
+ * P and the surrogate setting; game_load refuses (GAME_EINVAL) a file of a
+ * different shape or a truncated or foreign one. The training set itself
+ * is not stored: load into a handle created on the same data and settings.
+ * game_save writes `path`.tmp and renames it to `path`. Synchronous. */
+int game_save(game_t h, const char* path);
+int game_load(game_t h, const char* path);
+
 /* Per-stage device timing (CUDA events recorded on the handle's stream
  * around each kernel launch of the stages below). */
 typedef struct {
@@ -359,6 +370,35 @@ int game_batch_destroy(game_batch_t b);
  * expansion is psi_{b,j}(x) = sum_i phi_{b,j}(x_i) (K = B*d + 1).
  * Synchronises. */
 int game_gram(game_t h, double* G_out, double* b_out, double* yy_out);
+
+/* Outputs Out(m) of one chromosome (Eq. 2) on a set of patterns, computed
+ * in FP64 on the GPU (FP64 expansion, FP64 sum in gene order):
+ *   chrom [K] FP32 genes in the handle's layout (host or device);
+ *   X [M][N] FP32 features, row-major, host or device, with N the handle's;
+ *   NULL = the handle's training set (M must then equal its M);
+ *   out [M] FP64, host or device.
+ * M = 0 is allowed (nothing to do). The Chebyshev polynomials are evaluated
+ * by their recurrence at any x (the [-1, 1] check applies to the training
+ * set only). Host outputs synchronise; a device out only enqueues. */
+int game_predict(game_t h, const float* chrom, const float* X, int64_t M,
+                 double* out);
+
+/* Binary classification by one chromosome. Section 5 reports accuracy,
+ * completeness and contamination without defining them; here a pattern is
+ * a positive when its target y_m > threshold and is predicted positive when
+ * Out(m) > threshold (Out in FP64 as game_predict), and
+ *   accuracy = (tp + tn) / M, completeness = tp / (tp + fn),
+ *   contamination = fp / (tp + fp)   (0 when a denominator is 0). */
+typedef struct {
+  int64_t tp, fp, tn, fn;
+  double accuracy, completeness, contamination;
+} game_confusion;
+
+/* X [M][N], y [M] FP32 (host or device; both NULL = the training set, M
+ * then equal to its M); chrom [K] as game_predict; *out on the host.
+ * Synchronous. */
+int game_classify(game_t h, const float* chrom, const float* X, const float* y,
+                  int64_t M, double threshold, game_confusion* out);
 
 /* Waits for the handle's stream and reports a kernel timeout, if any. */
 int game_sync(game_t h);

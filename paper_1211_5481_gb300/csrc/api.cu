@@ -214,7 +214,7 @@ int ensure_gram(game_ctx* h) {
       dev_alloc(&h->gyy, 1) != cudaSuccess ||
       dev_alloc(&h->gpart, (size_t)gram_small_parts(gs) * kMaxRescore) != cudaSuccess ||
       dev_alloc(&phi, (size_t)rows * K) != cudaSuccess ||
-      dev_alloc(&part, (size_t)kGramSplits * K * K) != cudaSuccess) {
+      dev_alloc(&part, (size_t)gram_part_doubles(gs, h->num_sms)) != cudaSuccess) {
     cudaGetLastError();
     dev_free(phi);
     dev_free(part);
@@ -225,7 +225,8 @@ int ensure_gram(game_ctx* h) {
     h->gb = h->gyy = nullptr;
     return fail(GAME_ENOMEM, "Gram matrix");
   }
-  cudaError_t e = launch_gram_build(gs, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->st);
+  cudaError_t e = launch_gram_build(gs, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->num_sms,
+                                    h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dev_free(phi);
   dev_free(part);
@@ -1160,6 +1161,281 @@ int game_gram(game_t h, double* G_out, double* b_out, double* yy_out) {
   if (b_out) CK(cudaMemcpyAsync(b_out, h->gb, (size_t)K * sizeof(double), cudaMemcpyDefault, h->st));
   if (yy_out) CK(cudaMemcpyAsync(yy_out, h->gyy, sizeof(double), cudaMemcpyDefault, h->st));
   return check_status(h);
+}
+
+namespace {
+
+// Device copy of a host or device array for the duration of one call.
+struct DevCopy {
+  void* p = nullptr;
+  bool owned = false;
+  ~DevCopy() {
+    if (owned) cudaFree(p);
+  }
+};
+
+int dev_view(game_ctx* h, const void* src, size_t bytes, DevCopy* out) {
+  if (!src || bytes == 0) return GAME_OK;
+  if (is_device_ptr(src)) {
+    out->p = const_cast<void*>(src);
+    return GAME_OK;
+  }
+  if (cudaMalloc(&out->p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    out->p = nullptr;
+    return fail(GAME_ENOMEM, "device copy of a caller array");
+  }
+  out->owned = true;
+  CK(cudaMemcpyAsync(out->p, src, bytes, cudaMemcpyHostToDevice, h->st));
+  return GAME_OK;
+}
+
+// Shared argument handling of game_predict / game_classify: the chromosome
+// and the patterns (the training set when X is NULL) on the device.
+int predict_inputs(game_ctx* h, const float* chrom, const float* X, const float* y, int64_t M,
+                   bool need_y, DevCopy* dchrom, DevCopy* dX, DevCopy* dy, bool* tiled) {
+  if (!chrom) return fail(GAME_EINVAL, "chrom is NULL");
+  if (M < 0) return fail(GAME_EINVAL, "M must be >= 0");
+  if (!X) {
+    if (need_y && y) return fail(GAME_EINVAL, "X and y must both be given or both be NULL");
+    if (M != h->s.M) return fail(GAME_EINVAL, "M must equal the training set's M when X is NULL");
+    *tiled = true;
+  } else {
+    if (need_y && !y) return fail(GAME_EINVAL, "y is NULL");
+    *tiled = false;
+  }
+  int rc = dev_view(h, chrom, (size_t)h->Kg * sizeof(float), dchrom);
+  if (!rc && X) rc = dev_view(h, X, (size_t)M * h->s.N * sizeof(float), dX);
+  if (!rc && X && need_y) rc = dev_view(h, y, (size_t)M * sizeof(float), dy);
+  return rc;
+}
+
+}  // namespace
+
+int game_predict(game_t h, const float* chrom, const float* X, int64_t M, double* out) {
+  g_last_error.clear();
+  if (!h || !out) return fail(GAME_EINVAL, "NULL argument");
+  DevCopy dchrom, dX, dy, dout;
+  bool tiled = false;
+  int rc = predict_inputs(h, chrom, X, nullptr, M, false, &dchrom, &dX, &dy, &tiled);
+  if (rc) return rc;
+  if (M == 0) return GAME_OK;
+  const bool dev_out = is_device_ptr(out);
+  if (dev_out) {
+    dout.p = out;
+  } else if (cudaMalloc(&dout.p, (size_t)M * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    dout.p = nullptr;
+    return fail(GAME_ENOMEM, "device outputs");
+  } else {
+    dout.owned = true;
+  }
+  const float* Xd = tiled ? h->Xt : static_cast<const float*>(dX.p);
+  CK(launch_predict(h->s, h->prm.tied, h->Kg, Xd, tiled, M, static_cast<const float*>(dchrom.p),
+                    nullptr, 0.0, static_cast<double*>(dout.p), nullptr, h->num_sms, h->st));
+  if (dev_out && !dchrom.owned && !dX.owned) return GAME_OK;   // enqueued only
+  if (!dev_out)
+    CK(cudaMemcpyAsync(out, dout.p, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));   // before the temporary copies are freed
+  return check_status(h);
+}
+
+int game_classify(game_t h, const float* chrom, const float* X, const float* y, int64_t M,
+                  double threshold, game_confusion* out) {
+  g_last_error.clear();
+  if (!h || !out) return fail(GAME_EINVAL, "NULL argument");
+  if (threshold != threshold) return fail(GAME_EINVAL, "threshold is NaN");
+  DevCopy dchrom, dX, dy, dcnt;
+  bool tiled = false;
+  int rc = predict_inputs(h, chrom, X, y, M, true, &dchrom, &dX, &dy, &tiled);
+  if (rc) return rc;
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  if (M > 0) {
+    if (cudaMalloc(&dcnt.p, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      dcnt.p = nullptr;
+      return fail(GAME_ENOMEM, "counters");
+    }
+    dcnt.owned = true;
+    CK(cudaMemsetAsync(dcnt.p, 0, 4 * sizeof(unsigned long long), h->st));
+    const float* Xd = tiled ? h->Xt : static_cast<const float*>(dX.p);
+    const float* yd = tiled ? h->y : static_cast<const float*>(dy.p);
+    CK(launch_predict(h->s, h->prm.tied, h->Kg, Xd, tiled, M,
+                      static_cast<const float*>(dchrom.p), yd, threshold, nullptr,
+                      static_cast<unsigned long long*>(dcnt.p), h->num_sms, h->st));
+    CK(cudaMemcpyAsync(cnt, dcnt.p, sizeof(cnt), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    rc = check_status(h);
+    if (rc) return rc;
+  }
+  out->tp = (int64_t)cnt[0];
+  out->fp = (int64_t)cnt[1];
+  out->tn = (int64_t)cnt[2];
+  out->fn = (int64_t)cnt[3];
+  const int64_t total = out->tp + out->fp + out->tn + out->fn;
+  out->accuracy = total ? (double)(out->tp + out->tn) / (double)total : 0.0;
+  out->completeness = out->tp + out->fn ? (double)out->tp / (double)(out->tp + out->fn) : 0.0;
+  out->contamination = out->tp + out->fp ? (double)out->fp / (double)(out->tp + out->fp) : 0.0;
+  return GAME_OK;
+}
+
+namespace {
+
+// ---- checkpoint file ----
+// Layout (host byte order): CkptHeader, pop [P][K] FP32, fit [P] FP64; with
+// the surrogate, then w, m, v [n] FP32, trust [2] int32, trust_r FP32, the
+// replay ring rX [2][P][K] FP32 and rfit [2][P] FP64.
+constexpr char kCkptMagic[8] = {'G', 'A', 'M', 'E', 'C', 'K', 'P', '1'};
+
+struct CkptHeader {
+  char magic[8];
+  int64_t M, generation, sur_step, sur_params;
+  uint64_t seed;
+  int32_t N, degree, basis, tied, K, P, surrogate, ring_n, ring_head, last_n;
+};
+
+struct File {
+  FILE* f = nullptr;
+  ~File() {
+    if (f) fclose(f);
+  }
+};
+
+// host staging of one device array, written to / read from the file
+int dump(game_ctx* h, FILE* f, const void* dev, size_t bytes) {
+  std::vector<char> buf(bytes);
+  CK(cudaMemcpyAsync(buf.data(), dev, bytes, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (fwrite(buf.data(), 1, bytes, f) != bytes) return fail(GAME_EINVAL, "checkpoint write failed");
+  return GAME_OK;
+}
+
+int undump(game_ctx* h, FILE* f, void* dev, size_t bytes) {
+  std::vector<char> buf(bytes);
+  if (fread(buf.data(), 1, bytes, f) != bytes) return fail(GAME_EINVAL, "checkpoint truncated");
+  CK(cudaMemcpyAsync(dev, buf.data(), bytes, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return GAME_OK;
+}
+
+CkptHeader header_of(const game_ctx* h) {
+  CkptHeader c;
+  memset(&c, 0, sizeof(c));
+  memcpy(c.magic, kCkptMagic, 8);
+  c.M = h->s.M;
+  c.generation = h->gen;
+  c.seed = h->prm.seed;
+  c.N = h->s.N;
+  c.degree = h->s.d;
+  c.basis = h->s.basis;
+  c.tied = h->prm.tied;
+  c.K = h->Kg;
+  c.P = h->prm.P;
+  c.surrogate = h->prm.surrogate;
+  if (h->prm.surrogate) {
+    c.sur_step = h->sd.step;
+    c.sur_params = surrogate_param_count(h->Kg);
+    c.ring_n = h->ring_n;
+    c.ring_head = h->ring_head;
+    c.last_n = h->last_n;
+  }
+  return c;
+}
+
+}  // namespace
+
+int game_save(game_t h, const char* path) {
+  g_last_error.clear();
+  if (!h || !path) return fail(GAME_EINVAL, "NULL argument");
+  if (!h->fit_valid) {
+    int rc = eval_state(h);
+    if (rc) return rc;
+    h->fit_valid = true;
+  }
+  CK(cudaStreamSynchronize(h->st));
+  int rc = check_status(h);
+  if (rc) return rc;
+  const std::string tmp = std::string(path) + ".tmp";
+  File file;
+  file.f = fopen(tmp.c_str(), "wb");
+  if (!file.f) return fail(GAME_EINVAL, "cannot open the checkpoint file for writing");
+  const CkptHeader c = header_of(h);
+  const size_t P = (size_t)h->prm.P, K = (size_t)h->Kg;
+  if (fwrite(&c, sizeof(c), 1, file.f) != 1) return fail(GAME_EINVAL, "checkpoint write failed");
+  rc = dump(h, file.f, h->pop[h->cur], P * K * sizeof(float));
+  if (!rc) rc = dump(h, file.f, h->fit, P * sizeof(double));
+  if (!rc && h->prm.surrogate) {
+    const size_t n = (size_t)c.sur_params * sizeof(float);
+    rc = dump(h, file.f, h->sd.w, n);
+    if (!rc) rc = dump(h, file.f, h->sd.m, n);
+    if (!rc) rc = dump(h, file.f, h->sd.v, n);
+    if (!rc) rc = dump(h, file.f, h->trust, 2 * sizeof(int));
+    if (!rc) rc = dump(h, file.f, h->trust_r, sizeof(float));
+    for (int i = 0; i < 2 && !rc; ++i) rc = dump(h, file.f, h->rX[i], P * K * sizeof(float));
+    for (int i = 0; i < 2 && !rc; ++i) rc = dump(h, file.f, h->rfit[i], P * sizeof(double));
+  }
+  if (rc) return rc;
+  if (fclose(file.f) != 0) {
+    file.f = nullptr;
+    return fail(GAME_EINVAL, "checkpoint write failed");
+  }
+  file.f = nullptr;
+  if (rename(tmp.c_str(), path) != 0) return fail(GAME_EINVAL, "cannot move the checkpoint in place");
+  return GAME_OK;
+}
+
+int game_load(game_t h, const char* path) {
+  g_last_error.clear();
+  if (!h || !path) return fail(GAME_EINVAL, "NULL argument");
+  File file;
+  file.f = fopen(path, "rb");
+  if (!file.f) return fail(GAME_EINVAL, "cannot open the checkpoint file");
+  CkptHeader c;
+  if (fread(&c, sizeof(c), 1, file.f) != 1) return fail(GAME_EINVAL, "checkpoint truncated");
+  const CkptHeader mine = header_of(h);
+  if (memcmp(c.magic, kCkptMagic, 8) != 0) return fail(GAME_EINVAL, "not a GAME checkpoint");
+  if (c.M != mine.M || c.N != mine.N || c.degree != mine.degree || c.basis != mine.basis ||
+      c.tied != mine.tied || c.K != mine.K || c.P != mine.P || c.surrogate != mine.surrogate ||
+      (c.surrogate && c.sur_params != mine.sur_params))
+    return fail(GAME_EINVAL, "checkpoint of a different shape or settings");
+  if (c.generation < 0 || c.generation >= 0xFFFFFFFFll ||
+      (c.surrogate && (c.ring_n < 0 || c.ring_n > 2 || c.ring_head < 0 || c.ring_head > 1 ||
+                       c.sur_step < 0 || c.last_n < 0)))
+    return fail(GAME_EINVAL, "corrupt checkpoint header");
+  const size_t P = (size_t)h->prm.P, K = (size_t)h->Kg;
+  // the whole file is checked for its length before any state is replaced
+  size_t want = sizeof(CkptHeader) + P * K * sizeof(float) + P * sizeof(double);
+  if (c.surrogate)
+    want += 3 * (size_t)c.sur_params * sizeof(float) + 2 * sizeof(int) + sizeof(float) +
+            2 * P * K * sizeof(float) + 2 * P * sizeof(double);
+  if (fseek(file.f, 0, SEEK_END) != 0 || ftell(file.f) != (long)want ||
+      fseek(file.f, (long)sizeof(CkptHeader), SEEK_SET) != 0)
+    return fail(GAME_EINVAL, "checkpoint of the wrong length");
+  int rc = undump(h, file.f, h->pop[h->cur], P * K * sizeof(float));
+  if (!rc) rc = undump(h, file.f, h->fit, P * sizeof(double));
+  if (!rc && c.surrogate) {
+    const size_t n = (size_t)c.sur_params * sizeof(float);
+    rc = undump(h, file.f, h->sd.w, n);
+    if (!rc) rc = undump(h, file.f, h->sd.m, n);
+    if (!rc) rc = undump(h, file.f, h->sd.v, n);
+    if (!rc) rc = undump(h, file.f, h->trust, 2 * sizeof(int));
+    if (!rc) rc = undump(h, file.f, h->trust_r, sizeof(float));
+    for (int i = 0; i < 2 && !rc; ++i) rc = undump(h, file.f, h->rX[i], P * K * sizeof(float));
+    for (int i = 0; i < 2 && !rc; ++i) rc = undump(h, file.f, h->rfit[i], P * sizeof(double));
+    if (!rc) {
+      h->sd.step = c.sur_step;
+      h->ring_n = c.ring_n;
+      h->ring_head = c.ring_head;
+      h->last_n = c.last_n;
+    }
+  }
+  if (rc) {
+    h->fit_valid = false;   // state partly replaced: re-evaluated before use
+    return rc;
+  }
+  h->fit_valid = true;
+  h->gen = c.generation;
+  return GAME_OK;
 }
 
 int game_sync(game_t h) {

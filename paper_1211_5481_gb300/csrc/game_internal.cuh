@@ -161,13 +161,14 @@ cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int
                             const double* fit_kept, float* r_out, int* trusted, cudaStream_t st);
 
 // gram.cu -- the Gram form of the MSE (FP64)
-constexpr int kGramSplits = 8;   // row splits of a chunk's G accumulation
 int64_t gram_chunk_rows(const Shape& s);
+// doubles of the build's partial-sum scratch
+int64_t gram_part_doubles(const Shape& s, int num_sms);
 // G [K][K], b [K], yy [1] of the training set; phi_chunk [gram_chunk_rows][K]
-// and part [kGramSplits][K][K] are scratch.
+// and part [gram_part_doubles] are scratch.
 cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, double* G,
                               double* b, double* yy, double* phi_chunk, double* part,
-                              cudaStream_t st);
+                              int num_sms, cudaStream_t st);
 // fit of the P chromosomes pop [P][K] (idx NULL), or of rows idx[0..P-1]
 // written to fit[idx[p]]; err GAME_ERR_MSE or GAME_ERR_RMSE
 cudaError_t launch_gram_fitness(const Shape& s, const float* pop, int P, const int* idx,
@@ -179,6 +180,14 @@ int gram_small_parts(const Shape& s);
 cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const int* idx,
                                 const double* G, const double* b, const double* yy,
                                 double* part, double* fit, int err, cudaStream_t st);
+
+// predict.cu: Out(m) of chrom [Kg] in FP64 for M patterns of X (tiled: the
+// handle's [Mpad/128][N][128] layout, else row-major [M][N]) into out (may be
+// NULL); with counts (may be NULL) adds {TP, FP, TN, FN} against y
+cudaError_t launch_predict(const Shape& s, int tied, int Kg, const float* X, bool tiled,
+                           int64_t M, const float* chrom, const float* y, double threshold,
+                           double* out, unsigned long long* counts, int num_sms,
+                           cudaStream_t st);
 
 // api.cu
 void record_error(const char* msg);

@@ -19,10 +19,12 @@
 //
 // Accumulation: the patterns are taken in chunks of up to kChunk; a chunk's
 // design matrix Phi [mc][K] (FP64) is written by expand_kernel, then
-// gram_accum_kernel adds Phi^T Phi into the upper triangle of G (64 x 64
-// tiles, each thread a 4 x 4 block, the chunk's rows in order) and
-// vec_accum_kernel adds Phi^T y and y^T y. Every sum runs in a fixed order
-// (chunks in sequence, rows in order within a chunk), so G is reproducible.
+// gram_accum_kernel forms Phi^T Phi on the upper triangle (64 x 64 tiles,
+// each thread a 4 x 4 block) over up to 32 row ranges of the chunk, each in
+// row order, and gram_add_kernel adds the ranges' sums to G in range order;
+// vec_accum_kernel / vec_add_kernel do the same for Phi^T y and y^T y over 64
+// row ranges. Every sum runs in a fixed order (chunks in sequence, ranges
+// in order, rows in order within a range), so G is reproducible.
 // The quadratic forms: quad_kernel, one CTA per 8 chromosomes, thread t owns
 // rows t, t + 256, ... of G a_p and reads G column-wise (G is symmetric, so
 // G[k2][k1] over k2 is a coalesced column read), then a fixed-order CTA sum.
@@ -36,6 +38,7 @@ namespace {
 
 constexpr int kGT = 64;        // G tile
 constexpr int kQuadGroup = 8;  // chromosomes per quad CTA at most
+constexpr int kVecSplits = 64; // row splits of a chunk's b and y.y sums
 
 // Phi[r][k] for patterns m0 + r (r < mc), FP64; column 0 is 1.
 __global__ void expand_kernel(int64_t m0, int mc, int N, int d, int basis, int K,
@@ -180,24 +183,36 @@ __global__ void gram_add_kernel(int K, int splits, const double* __restrict__ pa
   }
 }
 
-// b[k] += sum_r Phi[r][k] y[m0 + r]; yy += sum_r y^2 (thread 0 of block 0)
-__global__ void vec_accum_kernel(int64_t m0, int mc, int K, const double* __restrict__ Phi,
-                                 const float* __restrict__ y, double* __restrict__ b,
-                                 double* __restrict__ yy) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < K) {
+// vpart[z][k] = sum over the rows r of split z (in order) of Phi[r][k] y[m0 + r]
+// for k < K, and vpart[z][K] = sum of y[m0 + r]^2; split z = blockIdx.y
+// takes rows [z rs, (z + 1) rs). Threads of a block read consecutive
+// columns of a row (coalesced).
+__global__ void vec_accum_kernel(int64_t m0, int mc, int rs, int K, const double* __restrict__ Phi,
+                                 const float* __restrict__ y, double* __restrict__ vpart) {
+  const int rlo = blockIdx.y * rs, rhi = min(mc, rlo + rs);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= K; k += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int r = 0; r < mc; ++r) s = fma(Phi[(int64_t)r * K + k], (double)y[m0 + r], s);
-    b[k] += s;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double s = 0.0;
-    for (int r = 0; r < mc; ++r) {
-      const double v = y[m0 + r];
-      s = fma(v, v, s);
+    if (k < K) {
+      for (int r = rlo; r < rhi; ++r) s = fma(Phi[(int64_t)r * K + k], (double)y[m0 + r], s);
+    } else {
+      for (int r = rlo; r < rhi; ++r) {
+        const double v = y[m0 + r];
+        s = fma(v, v, s);
+      }
     }
-    *yy += s;
+    vpart[(int64_t)blockIdx.y * (K + 1) + k] = s;
   }
+}
+
+// b[k] += sum over the splits, in order, of vpart[z][k]; yy likewise from column K.
+__global__ void vec_add_kernel(int K, int splits, const double* __restrict__ vpart,
+                               double* __restrict__ b, double* __restrict__ yy) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > K) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += vpart[(int64_t)z * (K + 1) + k];
+  if (k < K) b[k] += s;
+  else *yy += s;
 }
 
 // Lower triangle from the upper one.
@@ -326,15 +341,19 @@ quad_small_kernel(int n, int K, int ks, const float* __restrict__ pop, const int
   }
 }
 
+// One warp per candidate q: lane l adds parts l, l + 32, ... in order, then
+// a fixed xor-butterfly.
 __global__ void quad_small_finish(int n, int nparts, int64_t M, int err,
                                   const int* __restrict__ idx,
                                   const double* __restrict__ part, const double* __restrict__ yy,
                                   double* __restrict__ fit) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= n) return;
   double s = 0.0;
-  for (int j = 0; j < nparts; ++j) s += part[(int64_t)j * n + q];
-  fit[idx[q]] = finish_error((*yy + s) / (double)M, err);
+  for (int j = lane; j < nparts; j += 32) s += part[(int64_t)j * n + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) fit[idx[q]] = finish_error((*yy + s) / (double)M, err);
 }
 
 int blocks_for(int64_t n) {
@@ -346,6 +365,25 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
+// Row splits of a chunk's G accumulation: about three CTAs per SM over the
+// upper-triangle tiles, at most 32, and at most 1 GB of partial sums.
+int gram_splits(const Shape& s, int num_sms) {
+  const int KT = (s.K + kGT - 1) / kGT;
+  const int tiles = KT * (KT + 1) / 2;
+  int z = (3 * num_sms + tiles - 1) / tiles;
+  const int64_t cap = ((int64_t)1 << 30) / ((int64_t)s.K * s.K * 8);
+  if (z > cap) z = (int)cap;
+  if (z > 32) z = 32;
+  if (z < 1) z = 1;
+  return z;
+}
+
+int64_t gram_part_doubles(const Shape& s, int num_sms) {
+  const int64_t g = (int64_t)gram_splits(s, num_sms) * s.K * s.K;
+  const int64_t v = (int64_t)kVecSplits * (s.K + 1);
+  return g > v ? g : v;
+}
+
 int64_t gram_chunk_rows(const Shape& s) {
   // Phi chunk of at most 64k patterns and at most 256 MB
   int64_t rows = (int64_t)(256ll * 1024 * 1024) / ((int64_t)s.K * 8);
@@ -356,7 +394,7 @@ int64_t gram_chunk_rows(const Shape& s) {
 
 cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, double* G,
                               double* b, double* yy, double* phi_chunk, double* part,
-                              cudaStream_t st) {
+                              int num_sms, cudaStream_t st) {
   const int K = s.K;
   cudaError_t e = cudaMemsetAsync(G, 0, (size_t)K * K * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b, 0, (size_t)K * sizeof(double), st);
@@ -372,10 +410,14 @@ cudaError_t launch_gram_build(const Shape& s, const float* Xt, const float* y, d
     else
       expand_kernel<<<blocks_for((int64_t)mc * s.N), 256, 0, st>>>(m0, mc, s.N, s.d, s.basis,
                                                                   K, Xt, phi_chunk);
-    const int rs = (mc + kGramSplits - 1) / kGramSplits;
-    gram_accum_kernel<<<dim3(KT, KT, kGramSplits), 256, 0, st>>>(mc, rs, K, phi_chunk, part);
-    gram_add_kernel<<<blocks_for((int64_t)K * K), 256, 0, st>>>(K, kGramSplits, part, G);
-    vec_accum_kernel<<<(K + 255) / 256, 256, 0, st>>>(m0, mc, K, phi_chunk, y, b, yy);
+    const int zs = gram_splits(s, num_sms);
+    const int rs = (mc + zs - 1) / zs;
+    gram_accum_kernel<<<dim3(KT, KT, zs), 256, 0, st>>>(mc, rs, K, phi_chunk, part);
+    gram_add_kernel<<<blocks_for((int64_t)K * K), 256, 0, st>>>(K, zs, part, G);
+    const int vrs = (mc + kVecSplits - 1) / kVecSplits;
+    vec_accum_kernel<<<dim3((K + 256) / 256, kVecSplits), 256, 0, st>>>(m0, mc, vrs, K, phi_chunk,
+                                                                         y, part);
+    vec_add_kernel<<<(K + 256) / 256, 256, 0, st>>>(K, kVecSplits, part, b, yy);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -406,7 +448,7 @@ cudaError_t launch_gram_rescore(const Shape& s, const float* pop, int n, const i
   quad_small_kernel<<<dim3(bx, by), kSmallRows, smem, st>>>(n, s.K, ks, pop, idx, G, b, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  quad_small_finish<<<1, 32, 0, st>>>(n, bx * by, s.M, err, idx, part, yy, fit);
+  quad_small_finish<<<1, 32 * n, 0, st>>>(n, bx * by, s.M, err, idx, part, yy, fit);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,11 @@ synthetic sets stand in for it at its shape and beyond):
   workload.
 * ``surrogate_regression``: M=4,000,000, N=48 iid U[-1,1], additive degree-6
   Chebyshev target + N(0, 0.05^2) noise; degree 6 (K = 289), P = 2048.
+* ``small_classification``: the shape of the paper's own experiment
+  (Section 5: 2100 patterns, 11 columns of which two are the class, so 9
+  input features): M=2100, N=9 iid U[-1,1], labels +-1 = sign(t) of an
+  additive degree-3 Chebyshev polynomial with 5% flipped; fitted with the
+  trigonometric basis and shared genes (Eq. 5), P = B N + 1 = 19 (Eq. 4).
 
 The additive target t = c_0 + sum_i sum_{j=1..D} c_{ij} T_j(x_i) lies in the
 span of a Chebyshev chromosome of degree >= D, so with zero noise the
@@ -128,6 +133,17 @@ def large_classification(seed: int = 2, M: int = 1_000_000) -> Problem:
     lab[flip] = -lab[flip]
     return Problem(f"M{M}_N32_cheb8_P1024_cls", X, lab.astype(np.float32), 8, CHEB,
                    1024, 200, coef=coef, extra={"flip_rate": 0.05})
+
+
+def small_classification(seed: int = 5, M: int = 2100, N: int = 9) -> Problem:
+    X = _rng(seed, _TAG_X).uniform(-1.0, 1.0, size=(M, N)).astype(np.float32)
+    coef = _rng(seed, _TAG_COEF).uniform(-1.0, 1.0, size=N * 3 + 1).astype(np.float32)
+    t = additive_chebyshev_target(X, coef, 3)
+    lab = np.where(t >= 0.0, 1.0, -1.0)
+    flip = _rng(seed, _TAG_FLIP).random(M) < 0.05
+    lab[flip] = -lab[flip]
+    return Problem(f"M{M}_N{N}_gc_shape_cls", X, lab.astype(np.float32), 8, TRIG, 2 * N + 1,
+                   40000, coef=None, extra={"flip_rate": 0.05, "target_degree": 3})
 
 
 def surrogate_regression(seed: int = 4, M: int = 4_000_000) -> Problem:

@@ -48,7 +48,8 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_batch_get_tiles", "game_batch_fitness_ms", "game_batch_sync",
             "game_batch_destroy", "game_surrogate_predict", "game_surrogate_grad",
             "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
-            "game_surrogate_last", "game_gram")
+            "game_surrogate_last", "game_gram", "game_predict", "game_classify",
+            "game_save", "game_load")
 
 
 class GameError(RuntimeError):
@@ -95,6 +96,18 @@ class game_timing(ctypes.Structure):
         ("rescore_launches", ctypes.c_int64),
         ("surrogate_ms", ctypes.c_double),
         ("surrogate_launches", ctypes.c_int64),
+    ]
+
+
+class game_confusion(ctypes.Structure):
+    _fields_ = [
+        ("tp", ctypes.c_int64),
+        ("fp", ctypes.c_int64),
+        ("tn", ctypes.c_int64),
+        ("fn", ctypes.c_int64),
+        ("accuracy", ctypes.c_double),
+        ("completeness", ctypes.c_double),
+        ("contamination", ctypes.c_double),
     ]
 
 
@@ -163,6 +176,10 @@ def load(build_if_missing: bool = True):
         "game_surrogate_set_params": [vp, vp],
         "game_surrogate_last": [vp, vp, vp, ctypes.POINTER(i32), vp, vp],
         "game_gram": [vp, vp, vp, vp],
+        "game_predict": [vp, vp, vp, i64, dp],
+        "game_save": [vp, ctypes.c_char_p],
+        "game_load": [vp, ctypes.c_char_p],
+        "game_classify": [vp, vp, vp, vp, i64, ctypes.c_double, ctypes.POINTER(game_confusion)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -188,6 +205,11 @@ def _ptr(a):
         return a.ctypes.data
     assert a.is_contiguous(), "tensors must be contiguous"
     return a.data_ptr()
+
+
+def _f32(a):
+    """A contiguous float32 view of a numpy array; CUDA tensors pass as they are."""
+    return np.ascontiguousarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a
 
 
 def _stream_ptr(stream):
@@ -329,6 +351,34 @@ class Game:
         _check(load().game_gram(self.h, _ptr(G), _ptr(b), _ptr(yy)))
         return G, b, float(yy[0])
 
+    def predict(self, chrom, X=None):
+        """Outputs Out(m) (Eq. 2, FP64) of one chromosome on X [M][N] (numpy
+        or CUDA tensor; None = the training set)."""
+        chrom = _f32(chrom)
+        M = self.M if X is None else X.shape[0]
+        if X is not None and isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float32)
+        if X is None or isinstance(X, np.ndarray):
+            out = np.zeros(M, dtype=np.float64)
+        else:
+            import torch
+            out = torch.empty(M, dtype=torch.float64, device=X.device)
+        _check(load().game_predict(self.h, _ptr(chrom), _ptr(X), M, _ptr(out)))
+        return out
+
+    def classify(self, chrom, X=None, y=None, threshold=0.0):
+        """game_confusion of one chromosome on (X, y) (None = the training
+        set) as a dict."""
+        chrom = _f32(chrom)
+        M = self.M if X is None else X.shape[0]
+        if X is not None and isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float32)
+            y = np.ascontiguousarray(y, dtype=np.float32)
+        c = game_confusion()
+        _check(load().game_classify(self.h, _ptr(chrom), _ptr(X), _ptr(y), M, float(threshold),
+                                    ctypes.byref(c)))
+        return {name: getattr(c, name) for name, _ in game_confusion._fields_}
+
     # ---- fitness surrogate (numpy in / out) ----
     def surrogate_predict(self, pop):
         pop = np.ascontiguousarray(pop, dtype=np.float32)
@@ -384,6 +434,12 @@ class Game:
         fit = np.zeros(self.P, dtype=np.float64)
         g = game_get_population(self.h, pop, fit)
         return pop, fit, g
+
+    def save(self, path):
+        _check(load().game_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        _check(load().game_load(self.h, os.fsencode(path)))
 
     def set_state(self, pop, fit=None, generation=0):
         pop = np.ascontiguousarray(pop, dtype=np.float32) if isinstance(pop, np.ndarray) else pop

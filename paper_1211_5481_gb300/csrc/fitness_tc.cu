@@ -32,7 +32,8 @@
 //                drains fast, so the issuing path is kept minimal: precomputed
 //                descriptors, unrolled groups of four K=16 MMAs, K-blocks taken
 //                in pairs.
-//   warp 2       X producer: bulk-copies the next pattern tile's features.
+//   warp 2       X producer: bulk-copies the next pattern tile's features
+//                (staged mode only, below).
 //   warps 4-11   epilogue: tcgen05.ld of the accumulator (thread = chromosome
 //                = TMEM lane; warps 4-7 take the first half of the columns,
 //                8-11 the second), r = (y_m - a_0) - D, sse += r^2 in packed
@@ -40,11 +41,19 @@
 //   warps 12-15  expansion: each thread owns fixed pattern rows; per 8-column
 //                chunk (a table built once per launch says where the chunk
 //                starts in the feature / degree sequence) the basis
-//                recurrence runs in registers from the staged features, is
-//                rounded to BF16 and stored in the K-major SWIZZLE_128B
-//                operand layout. K-block kb of the next tile is written as
-//                soon as the last MMA reading K-block kb of this tile has
-//                completed, so the expansion overlaps the MMAs.
+//                recurrence runs in registers, is rounded to BF16 and stored
+//                in the K-major SWIZZLE_128B operand layout.
+// Expansion slots: the K-blocks of the tiles go, in order, into a ring of NS
+// K-block slots (use q = i * KB + kb takes slot q % NS); a slot is rewritten
+// as soon as the last MMA reading its previous use has completed. With
+// NS = KB this is one buffer per K-block; spare slots (NS > KB) let the next
+// tile's first K-blocks be written while this tile's MMAs still run.
+// Features: staged (the X producer bulk-copies the tile's feature blocks
+// into shared memory, the expansion reads them there) or, for the BF16 form
+// with Chebyshev runs of 8 degrees at 128 / 256 patterns, read by the
+// expansion threads from global memory (L2, prefetched two tiles ahead),
+// one K-block ahead of use; the shared memory this frees holds the spare
+// slots. Both modes produce identical expansion values.
 // PHI and D never leave the SM. All waits are bounded (2 s): on expiry the
 // kernel raises a status word, abandons its loops, waits for its own bulk
 // copies and MMAs in flight, frees tensor memory and returns.
@@ -76,6 +85,10 @@ struct TcArgs {
   int64_t M;
   int N, d, basis, Kp;
   int BN, KB, C, stages, nmma_last, ntiles, Ppad, tmem_cols;
+  int NS;       // expansion K-block slots (KB .. 2 KB): slots beyond KB let the
+                // next tile's first K-blocks be written while this tile's MMAs run
+  int xstage;   // 1: the tile's features are bulk-copied into shared memory;
+                // 0: read from global memory (L2) by the expansion warps
   const float* Xt;
   const float* y;
   const uint8_t* popA;
@@ -90,18 +103,19 @@ struct SmemPlan {
   int phi, ast, xs, cs, tab, bars, total;
 };
 
-__host__ __device__ inline int num_bars(int KB, int stages) { return 2 * stages + 2 * KB + 7; }
+__host__ __device__ inline int num_bars(int NS, int stages) { return 2 * stages + 2 * NS + 7; }
 
 // Byte offsets of the shared-memory regions from the 1024-aligned base.
-__host__ __device__ inline SmemPlan smem_plan(int KB, int BN, int N, int stages, int F) {
+__host__ __device__ inline SmemPlan smem_plan(int KB, int NS, int BN, int N, int stages, int F,
+                                              int xstage) {
   SmemPlan s;
   s.phi = 0;
-  s.ast = s.phi + KB * form_nphi(F) * BN * 128;
+  s.ast = s.phi + NS * form_nphi(F) * BN * 128;
   s.xs = s.ast + stages * form_na(F) * (int)kABytes;
-  s.cs = s.xs + N * BN * 4;
+  s.cs = s.xs + (xstage ? N * BN * 4 : 0);
   s.tab = s.cs + (F == kFormFP8 ? KB * 128 * 4 : 0);
   s.bars = (s.tab + KB * (form_cols(F) / 8) * 4 + 7) & ~7;
-  s.total = s.bars + num_bars(KB, stages) * 8 + 16 + 1024;   // + alignment slack
+  s.total = s.bars + num_bars(NS, stages) * 8 + 16 + 1024;   // + alignment slack
   return s;
 }
 
@@ -114,8 +128,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int BN = a.BN, KB = a.KB, N = a.N, S = a.stages;
-  const SmemPlan sp = smem_plan(KB, BN, N, S, F);
+  const int BN = a.BN, KB = a.KB, N = a.N, S = a.stages, NS = a.NS;
+  const SmemPlan sp = smem_plan(KB, NS, BN, N, S, F, a.xstage);
   uint8_t* phi = base + sp.phi;
   uint8_t* ast = base + sp.ast;
   float* xs = reinterpret_cast<float*>(base + sp.xs);
@@ -125,8 +139,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   uint64_t* a_full = bars;
   uint64_t* a_empty = a_full + S;
   uint64_t* phi_full = a_empty + S;
-  uint64_t* phi_free = phi_full + KB;
-  uint64_t* acc_full = phi_free + KB;
+  uint64_t* phi_free = phi_full + NS;
+  uint64_t* acc_full = phi_free + NS;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* x_full = acc_empty + 2;
   uint64_t* x_empty = x_full + 1;
@@ -140,9 +154,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       ptx::mbar_init(ptx::smem_addr(&a_full[s]), 1);
       ptx::mbar_init(ptx::smem_addr(&a_empty[s]), 1);
     }
-    for (int kb = 0; kb < KB; ++kb) {
-      ptx::mbar_init(ptx::smem_addr(&phi_full[kb]), kBasisThreads);
-      ptx::mbar_init(ptx::smem_addr(&phi_free[kb]), 1);
+    for (int sl = 0; sl < NS; ++sl) {
+      ptx::mbar_init(ptx::smem_addr(&phi_full[sl]), kBasisThreads);
+      ptx::mbar_init(ptx::smem_addr(&phi_free[sl]), 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_addr(&acc_full[b]), 1);
@@ -232,9 +246,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         }
       };
       // issues the MMAs of one K-block (nm of 4 K steps)
-      auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int nm) {
+      auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int slot, int nm) {
         const uint64_t ad = adesc0 + st * a_step;
-        const uint64_t bd = bdesc0 + (uint32_t)kb * b_step;
+        const uint64_t bd = bdesc0 + (uint32_t)slot * b_step;
         if (nm == 4) {
           kstep(d_tmem, ad, bd, kb != 0);
           kstep(d_tmem, ad + 2u, bd + 2u, 1u);
@@ -259,21 +273,25 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
               s1 = 0;
               ph1 ^= 1;
             }
+            // expansion slots of the two K-blocks: use q = it KB + kb of slot q % NS
+            const int q0 = it * KB + kb, q1 = q0 + 1;
+            const int sl0 = q0 % NS, sl1 = q1 % NS;
             // operands of both K-blocks first
             if (c == 0) {
-              ok = wait_bar(phi_full0 + 8 * kb, it & 1, abort_flag, a.status);
-              if (ok && two) ok = wait_bar(phi_full0 + 8 * (kb + 1), it & 1, abort_flag, a.status);
+              ok = wait_bar(phi_full0 + 8 * sl0, (q0 / NS) & 1, abort_flag, a.status);
+              if (ok && two)
+                ok = wait_bar(phi_full0 + 8 * sl1, (q1 / NS) & 1, abort_flag, a.status);
             }
             if (ok) ok = wait_bar(a_full0 + 8 * s, ph, abort_flag, a.status);
             if (ok && two) ok = wait_bar(a_full0 + 8 * s1, ph1, abort_flag, a.status);
             if (!ok) break;
-            kblock(d_tmem, s, kb, (kb == KB - 1) ? nlast : 4);
-            if (two) kblock(d_tmem, s1, kb + 1, (kb + 1 == KB - 1) ? nlast : 4);
+            kblock(d_tmem, s, kb, sl0, (kb == KB - 1) ? nlast : 4);
+            if (two) kblock(d_tmem, s1, kb + 1, sl1, (kb + 1 == KB - 1) ? nlast : 4);
             ptx::mma_commit(a_empty0 + 8 * s);
             if (two) ptx::mma_commit(a_empty0 + 8 * s1);
             if (c == a.C - 1) {
-              ptx::mma_commit(phi_free0 + 8 * kb);
-              if (two) ptx::mma_commit(phi_free0 + 8 * (kb + 1));
+              ptx::mma_commit(phi_free0 + 8 * sl0);
+              if (two) ptx::mma_commit(phi_free0 + 8 * sl1);
             }
             s = s1;
             ph = ph1;
@@ -294,8 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       wait_bar_drain(ptx::smem_addr(drain), 0, a.status);
     }
   } else if (warp == 2) {
-    // ---------------- X producer ----------------
-    if (lane == 0) {
+    // ---------------- X producer (staged features only) ----------------
+    if (lane == 0 && a.xstage) {
       int issued = 0;
       for (int it = 0; it < my_tiles; ++it) {
         const int64_t t = (int64_t)blockIdx.x + (int64_t)it * G;
@@ -541,11 +559,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
     // both rows of a Chebyshev chunk that stays in one feature's run of
     // degrees (the common case: degree 8): two interleaved recurrences, one
     // descriptor decode, no per-value branches
-    auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
-      const int i = (int)(desc & 0xFFFFu);
+    auto emit_run2x = [&](uint8_t* phik, uint32_t desc, int qd, float xa, float xb) {
       const int j0 = (int)((desc >> 16) & 31u);
-      const float xa = xr0[i * XW];
-      const float xb = R == 2 ? xr1[i * XW] : 0.f;
       const float a2 = xa + xa, b2 = xb + xb;
       float ta = xa, tam = 1.f, tb = xb, tbm = 1.f;
       for (int st = 1; st < j0; ++st) {
@@ -582,16 +597,90 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
             make_uint4(wb[0], wb[1], wb[2], wb[3]);
     };
+    auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
+      const int i = (int)(desc & 0xFFFFu);
+      emit_run2x(phik, desc, qd, xr0[i * XW], R == 2 ? xr1[i * XW] : 0.f);
+    };
+    // waits until expansion slot q % NS may be written (use q / NS)
+    auto slot_free = [&](int q) -> bool {
+      const int use = q / NS;
+      return use == 0 ||
+             wait_bar(ptx::smem_addr(&phi_free[q % NS]), (use - 1) & 1, abort_flag, a.status);
+    };
     bool ok = true;
-    for (int it = 0; it < my_tiles && ok; ++it) {
+    const bool staged = !(F == kFormBF16 && !TRI) || a.xstage;
+    if (!staged) {
+      // Features from global memory (L2), for the BF16 form, the Chebyshev
+      // basis with d a multiple of 8 (every chunk one feature's run of 8
+      // degrees) and BN a multiple of 128: the x of a K-block's 8 chunks
+      // are loaded one K-block ahead; thread 0 prefetches the next tile's
+      // feature blocks into L2.
+      auto xptr = [&](int itn, int r) -> const float* {
+        const int64_t m = ((int64_t)blockIdx.x + (int64_t)itn * G) * BN + r;
+        return a.Xt + (m >> 7) * (int64_t)N * kPatBlock + (m & (kPatBlock - 1));
+      };
+      auto prefetch_tile = [&](int itn) {
+        const int64_t m1 = ((int64_t)blockIdx.x + (int64_t)itn * G) * BN;
+        ptx::bulk_prefetch_l2(a.Xt + (m1 / kPatBlock) * N * kPatBlock,
+                              (uint32_t)((BN / kPatBlock) * N * kPatBlock * 4));
+      };
+      float na[8], nb[8];
+      auto load_kb = [&](int itn, int kbn) {
+        const float* p0 = xptr(itn, r0);
+        const float* p1 = xptr(itn, r1);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int i = (int)(tab[kbn * 8 + q] & 0xFFFFu);
+          na[q] = __ldg(p0 + i * kPatBlock);
+          nb[q] = R == 2 ? __ldg(p1 + i * kPatBlock) : 0.f;
+        }
+      };
+      if (bt == 0) {
+        if (my_tiles > 0) prefetch_tile(0);
+        if (my_tiles > 1) prefetch_tile(1);
+      }
+      if (my_tiles > 0) load_kb(0, 0);
+      for (int it = 0; it < my_tiles && ok; ++it) {
+        if (bt == 0 && it + 2 < my_tiles) prefetch_tile(it + 2);
+        for (int kb = 0; kb < KB; ++kb) {
+          float xa[8], xb[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            xa[q] = na[q];
+            xb[q] = nb[q];
+          }
+          if (kb + 1 < KB) load_kb(it, kb + 1);
+          else if (it + 1 < my_tiles) load_kb(it + 1, 0);
+          const int q = it * KB + kb;
+          ok = slot_free(q);
+          if (!ok) break;
+          uint8_t* phik = phi + (size_t)(q % NS) * BN * 128;
+#pragma unroll
+          for (int qd = 0; qd < 8; ++qd) {
+            const uint32_t desc = tab[kb * 8 + qd];
+            if (desc & kChunkZero) {
+              *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
+                  make_uint4(0u, 0u, 0u, 0u);
+              if (R == 2)
+                *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
+                    make_uint4(0u, 0u, 0u, 0u);
+            } else {
+              emit_run2x(phik, desc, qd, xa[qd], xb[qd]);
+            }
+          }
+          ptx::fence_proxy_async_smem();
+          ptx::mbar_arrive(ptx::smem_addr(&phi_full[q % NS]));
+        }
+      }
+    }
+    for (int it = 0; it < my_tiles && ok && staged; ++it) {
       ok = wait_bar(ptx::smem_addr(x_full), it & 1, abort_flag, a.status);
       if (!ok) break;
       for (int kb = 0; kb < KB; ++kb) {
-        if (it > 0) {
-          ok = wait_bar(ptx::smem_addr(&phi_free[kb]), (it - 1) & 1, abort_flag, a.status);
-          if (!ok) break;
-        }
-        uint8_t* phik = phi + (size_t)kb * NPHI * BN * 128;
+        const int q = it * KB + kb;
+        ok = slot_free(q);
+        if (!ok) break;
+        uint8_t* phik = phi + (size_t)(q % NS) * NPHI * BN * 128;
         if (F == kFormBF16 && !TRI) {
           for (int qd = q0; qd < 8; qd += QS) {
             const uint32_t desc = tab[kb * 8 + qd];
@@ -606,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int qd = q0; qd < 8; qd += QS) emit_unit(phik, kb, qd);
         }
         ptx::fence_proxy_async_smem();
-        ptx::mbar_arrive(ptx::smem_addr(&phi_full[kb]));
+        ptx::mbar_arrive(ptx::smem_addr(&phi_full[q % NS]));
       }
       if (!ok) break;
       ptx::mbar_arrive(ptx::smem_addr(x_empty));
@@ -632,19 +721,31 @@ TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
   const int cands[5] = {256, 192, 128, 64, 32};   // 192: BF16 form only
   // bf16x3 doubles both operands, so it may fall back to two gene stages
   const int min_stages = form == kFormBF16x3 ? 2 : 3;
+  // BF16 with Chebyshev runs of 8 degrees at 256 / 128 patterns: features
+  // read from L2 instead of staged, which frees room for spare expansion
+  // slots (the next tile's first K-blocks are written during this tile)
+  const bool runs = form == kFormBF16 && s.basis == GAME_BASIS_CHEB && s.d % 8 == 0;
+  auto take = [&](int BN, int NS, int stages, int xstage, int sm) {
+    pl.BN = BN;
+    pl.NS = NS;
+    pl.stages = stages;
+    pl.xstage = xstage;
+    // at least half an SM's shared memory: one CTA per SM, so the tensor
+    // memory allocation never waits on a co-resident CTA
+    pl.smem_bytes = sm < kMinSmem ? kMinSmem : sm;
+    pl.ok = true;
+  };
   for (int i = 0; i < 5 && !pl.ok; ++i) {
     if (cands[i] == 192 && form != kFormBF16) continue;
-    for (int stages = 4; stages >= min_stages; --stages) {
-      const int sm = smem_plan(pl.KB, cands[i], s.N, stages, form).total;
-      if (sm <= kMaxSmem) {
-        pl.BN = cands[i];
-        pl.stages = stages;
-        // at least half an SM's shared memory: one CTA per SM, so the tensor
-        // memory allocation never waits on a co-resident CTA
-        pl.smem_bytes = sm < kMinSmem ? kMinSmem : sm;
-        pl.ok = true;
-        break;
-      }
+    if (runs && cands[i] % 128 == 0)
+      for (int stages = 4; stages >= min_stages && !pl.ok; --stages)
+        for (int spare = pl.KB; spare >= 1 && !pl.ok; --spare) {
+          const int sm = smem_plan(pl.KB, pl.KB + spare, cands[i], s.N, stages, form, 0).total;
+          if (sm <= kMaxSmem) take(cands[i], pl.KB + spare, stages, 0, sm);
+        }
+    for (int stages = 4; stages >= min_stages && !pl.ok; --stages) {
+      const int sm = smem_plan(pl.KB, pl.KB, cands[i], s.N, stages, form, 1).total;
+      if (sm <= kMaxSmem) take(cands[i], pl.KB, stages, 1, sm);
     }
   }
   if (!pl.ok) return pl;
@@ -684,6 +785,8 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.KB = pl.KB;
   a.C = pl.C;
   a.stages = pl.stages;
+  a.NS = pl.NS;
+  a.xstage = pl.xstage;
   const int cols = form_cols(pl.form);
   const int last_cols = s.Kp - cols * (pl.KB - 1);
   a.nmma_last = (last_cols + cols / 4 - 1) / (cols / 4);
@@ -700,6 +803,10 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.status = status;
   if (pl.form == kFormFP8 && (!uscale || !colinv)) return cudaErrorInvalidValue;
   if (pl.BN == 192 && pl.form != kFormBF16) return cudaErrorInvalidValue;
+  if (pl.NS < pl.KB || pl.NS > 2 * pl.KB) return cudaErrorInvalidValue;
+  if (!pl.xstage && (pl.form != kFormBF16 || pl.BN % 128 != 0 || s.basis != GAME_BASIS_CHEB ||
+                     s.d % 8 != 0))
+    return cudaErrorInvalidValue;
   void (*kern)(const TcArgs) = err == GAME_ERR_MAE ? pick_kernel<true>(pl) : pick_kernel<false>(pl);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        pl.smem_bytes);

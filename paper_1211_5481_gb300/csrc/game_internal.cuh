@@ -78,7 +78,12 @@ __host__ __device__ constexpr int form_na(int f) { return f == kFormBF16x3 ? 2 :
 __host__ __device__ constexpr int form_nphi(int f) { return f == kFormBF16x3 ? 2 : 1; }
 // contraction columns per K-block (one 128-byte swizzled row)
 __host__ __device__ constexpr int form_cols(int f) { return f == kFormFP8 ? 128 : 64; }
-struct TcPlan { int form, BN, KB, NS, C, stages, grid, smem_bytes, tmem_cols, rows; bool ok; };
+// NS: expansion K-block slots (KB, or more with spare slots); xstage: 1 when
+// the features are staged in shared memory, 0 when read from L2
+struct TcPlan {
+  int form, BN, KB, NS, xstage, C, stages, grid, smem_bytes, tmem_cols, rows;
+  bool ok;
+};
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form);
 // err: GAME_ERR_MAE sums absolute residuals, any other value squared ones
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,

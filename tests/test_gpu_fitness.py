@@ -31,6 +31,11 @@ CASES = [
     (513, 64, 10, TRIG, 33),     # K' = 1280, the longest batched contraction
     (6000, 32, 8, CHEB, 256),    # the large classification shape, reduced M
     (3001, 48, 6, CHEB, 300),    # the surrogate workload's shape: 192-pattern tiles
+    # Chebyshev runs of 8 degrees (BF16: features from L2, spare expansion slots)
+    (1000, 5, 8, CHEB, 100),     # one K-block, zero chunks after K' = 40
+    (2999, 9, 8, CHEB, 130),     # K' = 72: the last MMA reads a zero chunk
+    (1500, 3, 16, CHEB, 64),     # degree 16: chunks starting at degree 9
+    (3000, 48, 8, CHEB, 200),    # K' = 384: 128-pattern tiles, ten slots
 ]
 
 

@@ -72,7 +72,7 @@ def parse():
 # DRAM bytes per launch of the dominant kernel, read + write, from the ncu
 # capture summarised in profiles/fitness_tc_M1000000_N32_cheb8_P1024_ncu.md
 # (valid for that kernel version and workload only; None elsewhere)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.72e6 + 3.45e6}
 
 
 def load_peaks():

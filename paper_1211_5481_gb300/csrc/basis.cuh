@@ -235,6 +235,66 @@ __device__ __forceinline__ void gen_chunk_x(uint32_t desc, int basis, int d, int
 }
 
 
+// Chebyshev chunk crossing feature runs, degree d >= 4 (so the chunk's 8
+// columns touch at most three features), for two patterns at once (va for
+// xrow0; vb for xrow1 when hasB): the same values, bit for bit, as gen_chunk,
+// with the three features' x loaded up front and both recurrences
+// interleaved. Columns from nvalid on are zero.
+__device__ __forceinline__ void cheb_cross2(uint32_t desc, int d, int N, const float* xrow0,
+                                            const float* xrow1, int xstride, bool hasB,
+                                            float (&va)[8], float (&vb)[8]) {
+  const int i = (int)(desc & 0xFFFFu);
+  const int j0 = (int)((desc >> 16) & 31u);
+  const int nvalid = (int)((desc >> 24) & 15u);
+  const int i1 = i + 1 < N ? i + 1 : N - 1, i2 = i + 2 < N ? i + 2 : N - 1;
+  const float xa0 = xrow0[i * xstride], xa1 = xrow0[i1 * xstride], xa2 = xrow0[i2 * xstride];
+  const float xb0 = hasB ? xrow1[i * xstride] : 0.f;
+  const float xb1 = hasB ? xrow1[i1 * xstride] : 0.f;
+  const float xb2 = hasB ? xrow1[i2 * xstride] : 0.f;
+  float a2 = xa0 + xa0, ta = xa0, tam = 1.f;
+  float b2 = xb0 + xb0, tb = xb0, tbm = 1.f;
+  for (int st = 1; st < j0; ++st) {
+    const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+    tam = ta;
+    ta = na;
+    tbm = tb;
+    tb = nb;
+  }
+  int j = j0;
+  bool second = false;   // the next restart takes the third feature
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    va[e] = ta;
+    vb[e] = tb;
+    if (j == d) {
+      j = 1;
+      const float xa = second ? xa2 : xa1, xb = second ? xb2 : xb1;
+      second = true;
+      a2 = xa + xa;
+      ta = xa;
+      tam = 1.f;
+      b2 = xb + xb;
+      tb = xb;
+      tbm = 1.f;
+    } else {
+      ++j;
+      const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+      tam = ta;
+      ta = na;
+      tbm = tb;
+      tb = nb;
+    }
+  }
+  if (nvalid < 8) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (e >= nvalid) {
+        va[e] = 0.f;
+        vb[e] = 0.f;
+      }
+  }
+}
+
 // The 8 expansion values of one chunk for one pattern whose features are
 // x_i = xrow[i * xstride] (shared or global memory).
 __device__ __forceinline__ void gen_chunk(uint32_t desc, int basis, int d, int N,

@@ -474,6 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           va[e] = ta;
           vb[e] = tb;
         }
+      } else if (cheb && a.d >= 4 && !(desc & kChunkZero)) {
+        cheb_cross2(desc, a.d, N, xrow0, xrow1, XW, hasB, va, vb);
       } else {
         gen_chunk(desc, a.basis, a.d, N, xrow0, XW, va);
         if (hasB) gen_chunk(desc, a.basis, a.d, N, xrow1, XW, vb);
@@ -597,6 +599,22 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
             make_uint4(wb[0], wb[1], wb[2], wb[3]);
     };
+    // both rows of a Chebyshev chunk that crosses feature runs (d >= 4)
+    auto emit_cheb_cross2 = [&](uint8_t* phik, uint32_t desc, int qd) {
+      float va[8], vb[8];
+      cheb_cross2(desc, a.d, N, xr0, xr1, XW, R == 2, va, vb);
+      uint32_t wa[4], wb[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        wa[h] = bf16x2_bits(va[2 * h], va[2 * h + 1]);
+        wb[h] = bf16x2_bits(vb[2 * h], vb[2 * h + 1]);
+      }
+      *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
+          make_uint4(wa[0], wa[1], wa[2], wa[3]);
+      if (R == 2)
+        *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
+            make_uint4(wb[0], wb[1], wb[2], wb[3]);
+    };
     auto emit_cheb_run2 = [&](uint8_t* phik, uint32_t desc, int qd) {
       const int i = (int)(desc & 0xFFFFu);
       emit_run2x(phik, desc, qd, xr0[i * XW], R == 2 ? xr1[i * XW] : 0.f);
@@ -686,6 +704,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
             const uint32_t desc = tab[kb * 8 + qd];
             if (cheb && (desc & kChunkRun) && ((desc >> 24) & 15u) == 8u) {
               emit_cheb_run2(phik, desc, qd);
+            } else if (cheb && a.d >= 4 && !(desc & kChunkZero)) {
+              emit_cheb_cross2(phik, desc, qd);
             } else {
               emit(phik, desc, qd, r0, xr0);
               if (R == 2) emit(phik, desc, qd, r1, xr1);

@@ -46,14 +46,19 @@ __global__ void init_population_kernel(uint64_t seed, int P, int K, float* __res
     pop[e] = ga::init_gene(seed, K, e);
 }
 
-// order[r] = the chromosome of rank r: a bitonic sort of (rank key, index)
-// over the next power of two >= P, padded with keys above every chromosome.
-__global__ void __launch_bounds__(kPlanThreads)
-ranking_order_kernel(int P, const double* __restrict__ fit, int* __restrict__ order) {
-  extern __shared__ __align__(16) uint64_t skey[];
+__host__ __device__ inline int pow2_at_least(int P) {
   int n2 = 1;
   while (n2 < P) n2 <<= 1;
-  int* sidx = reinterpret_cast<int*>(skey + n2);
+  return n2;
+}
+
+// order[r] = the chromosome of rank r (order may be NULL: the result stays in
+// sidx): a bitonic sort of (rank key, index) over the next power of two
+// >= P, padded with keys above every chromosome; skey [n2] and sidx [n2] in
+// shared memory.
+__device__ void ranking_sort_body(int P, const double* __restrict__ fit, uint64_t* skey,
+                                  int* sidx, int* __restrict__ order) {
+  const int n2 = pow2_at_least(P);
   for (int i = threadIdx.x; i < n2; i += kPlanThreads) {
     skey[i] = i < P ? ga::rank_key(fit[i]) : ga::kKeyMax;
     sidx[i] = i < P ? i : 0x7fffffff;
@@ -78,14 +83,20 @@ ranking_order_kernel(int P, const double* __restrict__ fit, int* __restrict__ or
       }
       __syncthreads();
     }
-  for (int i = threadIdx.x; i < P; i += kPlanThreads) order[i] = sidx[i];
+  if (order)
+    for (int i = threadIdx.x; i < P; i += kPlanThreads) order[i] = sidx[i];
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+ranking_order_kernel(int P, const double* __restrict__ fit, int* __restrict__ order) {
+  extern __shared__ __align__(16) uint64_t skey[];
+  ranking_sort_body(P, fit, skey, reinterpret_cast<int*>(skey + pow2_at_least(P)), order);
 }
 
 // cum[p + 1] = sum_{j<=p} roulette_weight(fit[j]), cum[0] = 0: each thread
 // sums a contiguous chunk, an exclusive scan of the chunk sums gives its
 // offset (integers, so the result does not depend on the order).
-__global__ void __launch_bounds__(kPlanThreads)
-roulette_cum_kernel(int P, const double* __restrict__ fit, uint64_t* __restrict__ cum) {
+__device__ void roulette_cum_body(int P, const double* __restrict__ fit, uint64_t* cum) {
   __shared__ uint64_t wsum[kPlanThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int chunk = (P + kPlanThreads - 1) / kPlanThreads;
@@ -119,6 +130,11 @@ roulette_cum_kernel(int P, const double* __restrict__ fit, uint64_t* __restrict_
 }
 
 __global__ void __launch_bounds__(kPlanThreads)
+roulette_cum_kernel(int P, const double* __restrict__ fit, uint64_t* __restrict__ cum) {
+  roulette_cum_body(P, fit, cum);
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
 ga_plan_kernel(GaDev g_, const double* __restrict__ fit, uint64_t seed, uint32_t g,
                int4* __restrict__ plan) {
   ga::plan_body(g_, fit, seed, g, plan);
@@ -131,6 +147,42 @@ __global__ void ga_breed_kernel(GaDev g_, const float* __restrict__ pop,
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     next[e] = ga::breed_gene(g_, pop, plan, seed, g, e);
+}
+
+// Small populations (P, Nout <= kFusedMax, Nout K <= kFusedGenes): the
+// selection table, the plan and every gene of the next population in one CTA
+// and one launch instead of three or four, with the table and the plan in
+// shared memory; the same device functions, so the same result bit for bit.
+constexpr int kFusedMax = 1024;
+constexpr int64_t kFusedGenes = 65536;
+
+__host__ __device__ inline int fused_table_bytes(const GaDev& ga) {
+  return ga.sel == GAME_SEL_RANKING    ? pow2_at_least(ga.P) * 12
+         : ga.sel == GAME_SEL_ROULETTE ? (ga.P + 1) * 8
+                                       : 0;
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+ga_fused_kernel(GaDev g_, const float* __restrict__ pop, const double* __restrict__ fit,
+                uint64_t seed, uint32_t g, float* __restrict__ next) {
+  extern __shared__ __align__(16) uint64_t fsm[];
+  GaDev ga = g_;
+  const int tb = (fused_table_bytes(g_) + 15) & ~15;
+  int4* plan = reinterpret_cast<int4*>(reinterpret_cast<char*>(fsm) + tb);
+  if (ga.sel == GAME_SEL_RANKING) {
+    int* sidx = reinterpret_cast<int*>(fsm + pow2_at_least(ga.P));
+    ranking_sort_body(ga.P, fit, fsm, sidx, nullptr);
+    ga.order = sidx;
+  } else if (ga.sel == GAME_SEL_ROULETTE) {
+    roulette_cum_body(ga.P, fit, fsm);
+    ga.cum = fsm;
+  }
+  __syncthreads();
+  ga::plan_body(ga, fit, seed, g, plan);
+  __syncthreads();
+  const int64_t n = (int64_t)ga.Nout * ga.K;
+  for (int64_t e = threadIdx.x; e < n; e += kPlanThreads)
+    next[e] = ga::breed_gene(ga, pop, plan, seed, g, e);
 }
 
 int blocks_for(int64_t n, int threads) {
@@ -157,6 +209,11 @@ cudaError_t launch_generation(const GaDev& ga, const float* pop, const double* f
                               uint64_t seed, uint32_t g, int4* plan, float* next,
                               cudaStream_t st) {
   if (ga.E > kMaxElites) return cudaErrorInvalidValue;
+  if (ga.P <= kFusedMax && ga.Nout <= kFusedMax && (int64_t)ga.Nout * ga.K <= kFusedGenes) {
+    const int smem = ((fused_table_bytes(ga) + 15) & ~15) + ga.Nout * (int)sizeof(int4);
+    ga_fused_kernel<<<1, kPlanThreads, smem, st>>>(ga, pop, fit, seed, g, next);
+    return cudaGetLastError();
+  }
   if (ga.sel == GAME_SEL_RANKING) {
     if (ga.P > kMaxRankingP || !ga.order) return cudaErrorInvalidValue;
     const int smem = ranking_smem_bytes(ga.P);

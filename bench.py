@@ -52,6 +52,9 @@ def parse():
                          "surrogate-screened offspring, against the plain FP32 form; paper: "
                          "the degree x iterations grid of Section 5 in the paper-literal "
                          "mode on a set of the paper's data shape")
+    ap.add_argument("--surrogate-steps", type=int, default=1, metavar="S",
+                    help="surrogate workload: Adam steps per generation on each stored "
+                         "generation (game_params.surrogate_steps)")
     ap.add_argument("--selection", choices=["ranking", "roulette"], default="ranking",
                     help="paper workload: parent selection (Section 5 names both)")
     ap.add_argument("--oracle-run", type=int, default=0, metavar="G",
@@ -341,7 +344,8 @@ def run_surrogate(args, torch, game, dev, world, rank):
         return sum(x.elapsed_time(y) for x, y in ev) / len(ev), tm
 
     gs = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=8)
+                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=8,
+                   surrogate_steps=args.surrogate_steps)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
     t_sur, tm = timed(gs, args.steps, max(args.warmup, 3))
     clk = clocks.stop()
@@ -370,7 +374,8 @@ def run_surrogate(args, torch, game, dev, world, rank):
         _, _, best_o = oracle.train(pr.X, pr.y, pr.degree, pr.basis, P, G, 4, use_gram=True)
         t_o = time.perf_counter() - t0
         gg = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=8)
+                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=8,
+                       surrogate_steps=args.surrogate_steps)
         gg.train(G)
         _, fit_g, _ = gg.population()
         gg.close()
@@ -388,6 +393,7 @@ def run_surrogate(args, torch, game, dev, world, rank):
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "form": "BF16 contraction + elite re-score + surrogate screening, 8x "
                            "oversampled offspring",
+                   "surrogate_steps": args.surrogate_steps,
                    "step": "one screened generation: offspring, MLP screening, exact "
                            "fitness of the kept population, MLP training",
                    "l2": "flushed between steps (256 MB write)"},

@@ -132,11 +132,15 @@ typedef struct {
   int32_t error;        /* GAME_ERR_* (default MSE). GAME_ERR_MAE has no
                            Gram form: it needs a direct precision
                            (not GAME_PREC_GRAM) and rescore_top = 0 */
-  int32_t reserved[2];  /* must be zero */
+  int32_t surrogate_steps; /* with the surrogate: Adam steps per generation
+                           on each of the last two generations' exact
+                           (chromosome, fitness) pairs, 1..64 (default 1) */
+  int32_t reserved[1];  /* must be zero */
 } game_params;
 
 /* Fills *out with the defaults listed above (and rescore_top = 8,
- * oversample = 8, tournament selection, per-feature genes, MSE). */
+ * oversample = 8, surrogate_steps = 1, tournament selection, per-feature
+ * genes, MSE). */
 int game_params_default(game_params* out);
 
 /* Creates a handle for one training set and copies it to the device.

@@ -468,7 +468,8 @@ int surrogate_step(game_ctx* h, const float* X, const double* fit, int n) {
 }
 
 // Adds the current population and its exact fitness to the replay ring and
-// trains one step on each stored generation, oldest first.
+// trains surrogate_steps rounds of one step on each stored generation,
+// oldest first.
 int surrogate_learn(game_ctx* h) {
   const int P = h->prm.P, K = h->Kg;
   const int slot = h->ring_head;
@@ -478,11 +479,12 @@ int surrogate_learn(game_ctx* h) {
                      cudaMemcpyDeviceToDevice, h->st));
   h->ring_head ^= 1;
   if (h->ring_n < 2) h->ring_n += 1;
-  for (int i = h->ring_n - 1; i >= 0; --i) {
-    const int sl = (slot - i + 2) % 2;
-    const int rc = surrogate_step(h, h->rX[sl], h->rfit[sl], P);
-    if (rc) return rc;
-  }
+  for (int rep = 0; rep < h->prm.surrogate_steps; ++rep)
+    for (int i = h->ring_n - 1; i >= 0; --i) {
+      const int sl = (slot - i + 2) % 2;
+      const int rc = surrogate_step(h, h->rX[sl], h->rfit[sl], P);
+      if (rc) return rc;
+    }
   return GAME_OK;
 }
 
@@ -591,6 +593,10 @@ int validate_params(const game_params& p, const Shape& s, std::string* why) {
     *why = "unknown error function";
     return 0;
   }
+  if (p.surrogate_steps < 0 || p.surrogate_steps > 64 || (p.surrogate && p.surrogate_steps < 1)) {
+    *why = "surrogate_steps must be in 1..64";
+    return 0;
+  }
   if (p.error == GAME_ERR_MAE && (p.precision == GAME_PREC_GRAM || p.rescore_top != 0)) {
     *why = "the MAE has no Gram form: use a direct precision and rescore_top = 0";
     return 0;
@@ -692,6 +698,7 @@ int game_params_default(game_params* out) {
   out->selection = GAME_SEL_TOURNAMENT;
   out->tied = 0;
   out->error = GAME_ERR_MSE;
+  out->surrogate_steps = 1;
   return GAME_OK;
 }
 

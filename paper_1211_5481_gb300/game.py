@@ -78,7 +78,8 @@ class game_params(ctypes.Structure):
         ("selection", ctypes.c_int32),
         ("tied", ctypes.c_int32),
         ("error", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("surrogate_steps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 

@@ -65,14 +65,16 @@ def test_host_side_argument_checks():
                          ctypes.byref(h))
     assert rc == game.GAME_EINVAL
     assert p.selection == game.GAME_SEL_TOURNAMENT and p.tied == 0
-    assert p.error == game.GAME_ERR_MSE
+    assert p.error == game.GAME_ERR_MSE and p.surrogate_steps == 1
     # selection, shared genes and error function settings
     for field, value, extra in [("selection", 3, {}), ("selection", -1, {}),
                                 ("selection", game.GAME_SEL_RANKING, {"P": 16385}),
                                 ("tied", 2, {}), ("error", 3, {}),
                                 ("error", game.GAME_ERR_MAE, {}),   # rescore_top = 8
                                 ("error", game.GAME_ERR_MAE,
-                                 {"rescore_top": 0, "precision": game.GAME_PREC_GRAM})]:
+                                 {"rescore_top": 0, "precision": game.GAME_PREC_GRAM}),
+                                ("surrogate_steps", 65, {}),
+                                ("surrogate_steps", 0, {"surrogate": 1})]:
         bad = game.game_params_default()
         setattr(bad, field, value)
         for k, v in extra.items():
@@ -81,7 +83,7 @@ def test_host_side_argument_checks():
                              ctypes.byref(h))
         assert rc == game.GAME_EINVAL, (field, value, extra)
     bad = game.game_params_default()
-    bad.reserved[1] = 1
+    bad.reserved[0] = 1
     rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
                          ctypes.byref(h))
     assert rc == game.GAME_EINVAL

@@ -295,6 +295,46 @@ __device__ __forceinline__ void cheb_cross2(uint32_t desc, int d, int N, const f
   }
 }
 
+// One-pattern form of cheb_cross2 (same values as gen_chunk).
+__device__ __forceinline__ void cheb_cross1(uint32_t desc, int d, int N, const float* xrow,
+                                            int xstride, float (&v)[8]) {
+  const int i = (int)(desc & 0xFFFFu);
+  const int j0 = (int)((desc >> 16) & 31u);
+  const int nvalid = (int)((desc >> 24) & 15u);
+  const int i1 = i + 1 < N ? i + 1 : N - 1, i2 = i + 2 < N ? i + 2 : N - 1;
+  const float x0 = xrow[i * xstride], x1 = xrow[i1 * xstride], x2 = xrow[i2 * xstride];
+  float a2 = x0 + x0, t = x0, tm = 1.f;
+  for (int st = 1; st < j0; ++st) {
+    const float n = fmaf(a2, t, -tm);
+    tm = t;
+    t = n;
+  }
+  int j = j0;
+  bool second = false;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    v[e] = t;
+    if (j == d) {
+      j = 1;
+      const float x = second ? x2 : x1;
+      second = true;
+      a2 = x + x;
+      t = x;
+      tm = 1.f;
+    } else {
+      ++j;
+      const float n = fmaf(a2, t, -tm);
+      tm = t;
+      t = n;
+    }
+  }
+  if (nvalid < 8) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (e >= nvalid) v[e] = 0.f;
+  }
+}
+
 // The 8 expansion values of one chunk for one pattern whose features are
 // x_i = xrow[i * xstride] (shared or global memory).
 __device__ __forceinline__ void gen_chunk(uint32_t desc, int basis, int d, int N,

@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           vb[e] = tb;
         }
       } else if (cheb && a.d >= 4 && !(desc & kChunkZero)) {
-        cheb_cross2(desc, a.d, N, xrow0, xrow1, XW, hasB, va, vb);
+        if (hasB) cheb_cross2(desc, a.d, N, xrow0, xrow1, XW, true, va, vb);
+        else cheb_cross1(desc, a.d, N, xrow0, XW, va);
       } else {
         gen_chunk(desc, a.basis, a.d, N, xrow0, XW, va);
         if (hasB) gen_chunk(desc, a.basis, a.d, N, xrow1, XW, vb);
@@ -602,7 +603,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
     // both rows of a Chebyshev chunk that crosses feature runs (d >= 4)
     auto emit_cheb_cross2 = [&](uint8_t* phik, uint32_t desc, int qd) {
       float va[8], vb[8];
-      cheb_cross2(desc, a.d, N, xr0, xr1, XW, R == 2, va, vb);
+      if (R == 2) cheb_cross2(desc, a.d, N, xr0, xr1, XW, true, va, vb);
+      else cheb_cross1(desc, a.d, N, xr0, XW, va);
       uint32_t wa[4], wb[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {

@@ -78,6 +78,26 @@ def parse():
 NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.72e6 + 3.45e6}
 
 
+def max_over_ranks(t, world, dev=None):
+    """The slowest rank's time, returned on every rank (t itself when there
+    is one rank): the all-reduce runs on dev for NCCL, on the host for gloo."""
+    if world <= 1:
+        return float(t)
+    import torch
+    import torch.distributed as dist
+    if dev is None or dist.get_backend() == "gloo":
+        dev = torch.device("cpu")
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank, t_step_s, world):
+    """Units processed by all ranks (the same per rank: weak scaling) per
+    second of the slowest rank's step."""
+    return units_per_rank * world / t_step_s
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,17 +287,14 @@ def run_batched(args, torch, game, dev, world, rank):
     b.sync()
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    t_step = sum(x.elapsed_time(y) for x, y in ev) / len(ev) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev) / len(ev) * 1e-3, world, dev)
     fit_ms = b.fitness_ms(10)
     peaks, peak_src = load_peaks()
     achieved = flops / (fit_ms * 1e-3) / 1e12
     peak = float(peaks["bf16_tflops"])
     line = {
-        "metric": METRIC, "value": evals * world / t_step, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(evals, t_step, world), "unit": UNIT,
+        "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
@@ -573,12 +590,8 @@ def main():
     clocks = ClockSampler(local, enabled=not args.no_clocks)
     step_ms, tm = timed_steps(g, args.steps, max(args.warmup, 3))
     clk = clocks.stop()
-    t_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = M * P * world / (t_step * 1e-3)
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    value = whole_job_rate(M * P, t_step * 1e-3, world)
 
     peaks, peak_src = load_peaks()
     flops_launch = 2.0 * M * P * (K - 1) + 3.0 * M * P

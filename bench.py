@@ -176,6 +176,38 @@ def oracle_sample_rate(pr, P_s, target_s=8.0, max_s=25.0):
                       f"direct-form FP64 fitness, {dt:.2f} s"}, M_s
 
 
+def oracle_extra(pr, M_s, cpu):
+    """The direct-form oracle on one core (a 1/cores sample), its estimated
+    time per generation of the whole workload on all cores, and the Gram
+    form (a different algorithm: G built once, then P K^2 per generation),
+    timed on a 100,000-pattern build scaled to M and one full generation."""
+    import oracle
+    cores = cpu["cores"]
+    P = pr.P
+    pop = oracle.init_population(2, 16, pr.K)
+    M_1 = max(2000, M_s // max(cores, 1))
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.fitness(pr.X[:M_1], pr.y[:M_1], pop, pr.degree, pr.basis)
+    t1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    M_g = min(pr.M, 100_000)
+    t0 = time.perf_counter()
+    gs = oracle.gram(pr.X[:M_g], pr.y[:M_g], pr.degree, pr.basis)
+    t_build = (time.perf_counter() - t0) * pr.M / M_g
+    popP = oracle.init_population(3, P, pr.K)
+    t0 = time.perf_counter()
+    oracle.fitness_gram(gs, popP)
+    t_gen = time.perf_counter() - t0
+    return {"one_core": {"value": M_1 * 16 / t1, "unit": UNIT, "cores": 1,
+                         "sample": f"first {M_1} patterns x 16 chromosomes"},
+            "direct_generation_s_all_cores": pr.M * P / cpu["value"],
+            "gram_form": {"build_s_estimate": t_build, "generation_s": t_gen,
+                          "note": "Gram form of the MSE: a different algorithm, G built "
+                                  f"once (timed on {M_g} patterns, scaled to M), then "
+                                  "P K^2 FP64 per generation"}}
+
+
 def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
     """Accuracy of every contraction form against the FP64 oracle, per
     generation of the GA run held by handle g: the current population is
@@ -292,6 +324,11 @@ def run_batched(args, torch, game, dev, world, rank):
     peaks, peak_src = load_peaks()
     achieved = flops / (fit_ms * 1e-3) / 1e12
     peak = float(peaks["bf16_tflops"])
+    # algorithmic bytes of one launch: features, targets, operand image, partials
+    nbytes = float(sum(4.0 * pr.M * pr.N + 4.0 * pr.M + 2.0 * pr.P * (pr.K - 1)
+                       + 8.0 * -(-pr.M // 128) * pr.P for pr in runs))
+    hbm_gbs = nbytes / (fit_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
     line = {
         "metric": METRIC, "value": whole_job_rate(evals, t_step, world), "unit": UNIT,
         "n_gpus": world,
@@ -312,6 +349,10 @@ def run_batched(args, torch, game, dev, world, rank):
                      "peak_source": f"{peak_src} bf16_tflops (burst)",
                      "kernel": "fitness_batch_kernel", "kernel_ms": fit_ms,
                      "flops_per_launch": flops},
+        "roofline_hbm": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hbm_gbs / hbm_peak, "algorithmic_bytes": nbytes,
+                         "note": "the same launch against the HBM roof (partials counted at "
+                                 "128-pattern tiles)"},
         "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
@@ -636,8 +677,17 @@ def main():
                         precision=game.GAME_PREC_FP32, seed=2)
         ms32, tm32 = timed_steps(g32, max(3, args.steps // 4), 3)
         t32 = sum(ms32) / len(ms32)
-        fp32_leg = {"value": M * P * world / (t32 * 1e-3), "ms_per_step": t32,
-                    "fitness_kernel_ms": tm32["fitness_ms"] / max(tm32["fitness_launches"], 1)}
+        k32 = tm32["fitness_ms"] / max(tm32["fitness_launches"], 1)
+        # CUDA-core FP32 peak: SMs x 128 FP32 lanes x 2 flop (FFMA) x max SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = float(clk.get("sm_max_mhz") or 2070.0)
+        ffma_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        a32 = (2.0 * M * P * (K - 1) + 3.0 * M * P) / (k32 * 1e-3) / 1e12
+        fp32_leg = {"value": whole_job_rate(M * P, t32 * 1e-3, world), "ms_per_step": t32,
+                    "fitness_kernel_ms": k32,
+                    "roofline": {"bound": "alu", "achieved": a32, "peak": ffma_peak,
+                                 "unit": "TFLOP/s", "frac": a32 / ffma_peak,
+                                 "peak_source": f"{sms} SMs x 128 FFMA lanes x 2 x {mhz:.0f} MHz"}}
         g32.close()
 
     # end to end through the public API: a host population (pinned) in, its
@@ -678,7 +728,8 @@ def main():
                "fp32_max_rel_err": float(np.max(np.abs(f_32[sample] - ref) / ref)),
                "top10_agreement_form_vs_fp32": len(set(np.argsort(f_bf)[:10]) &
                                                     set(np.argsort(f_32)[:10])) / 10}
-        cpu, _ = oracle_sample_rate(pr, 16)
+        cpu, M_s = oracle_sample_rate(pr, 16)
+        cpu.update(oracle_extra(pr, M_s, cpu))
         if args.precision_report > 0:
             acc["precision_forms"] = precision_report(game, g, pr, args.precision_report)
 

@@ -266,8 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           if (!ok) break;
           ptx::tc_fence_after();
           const uint32_t d_tmem = tmem + buf * (uint32_t)BN;
-          for (int kb = 0; kb < KB && ok; kb += 2) {
-            const bool two = kb + 1 < KB;
+          // the first chromosome tile of a pattern tile takes K-blocks one at a
+          // time, so its MMAs start as soon as the first expansion slot is full
+          for (int kb = 0; kb < KB && ok; kb += (c != 0 && kb + 1 < KB) ? 2 : 1) {
+            const bool two = c != 0 && kb + 1 < KB;
             uint32_t s1 = s + 1, ph1 = ph;
             if (s1 == (uint32_t)S) {
               s1 = 0;

@@ -75,7 +75,7 @@ def parse():
 # DRAM bytes per launch of the dominant kernel, read + write, from the ncu
 # capture summarised in profiles/fitness_tc_M1000000_N32_cheb8_P1024_ncu.md
 # (valid for that kernel version and workload only; None elsewhere)
-NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.72e6 + 3.45e6}
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.71e6 + 3.09e6}
 
 
 def max_over_ranks(t, world, dev=None):

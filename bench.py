@@ -52,6 +52,8 @@ def parse():
                          "surrogate-screened offspring, against the plain FP32 form; paper: "
                          "the degree x iterations grid of Section 5 in the paper-literal "
                          "mode on a set of the paper's data shape")
+    ap.add_argument("--error", choices=["mse", "rmse", "mae"], default="mse",
+                    help="classification workload: the fitness's error function (Section 3)")
     ap.add_argument("--surrogate-steps", type=int, default=1, metavar="S",
                     help="surrogate workload: Adam steps per generation on each stored "
                          "generation (game_params.surrogate_steps)")
@@ -597,8 +599,10 @@ def main():
             "bf16x3": game.GAME_PREC_BF16X3, "fp8": game.GAME_PREC_FP8,
             "gram": game.GAME_PREC_GRAM}[args.form]
     tensor = prec not in (game.GAME_PREC_FP32, game.GAME_PREC_GRAM)
+    errk = {"mse": game.GAME_ERR_MSE, "rmse": game.GAME_ERR_RMSE, "mae": game.GAME_ERR_MAE}[args.error]
+    ekw = dict(error=errk, rescore_top=0 if args.error == "mae" else 8)
     t_create = time.perf_counter()
-    g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2)
+    g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2, **ekw)
     t_create = time.perf_counter() - t_create
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -674,7 +678,7 @@ def main():
     fp32_leg = None
     if tensor and not args.no_fp32_leg:
         g32 = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P,
-                        precision=game.GAME_PREC_FP32, seed=2)
+                        precision=game.GAME_PREC_FP32, seed=2, **ekw)
         ms32, tm32 = timed_steps(g32, max(3, args.steps // 4), 3)
         t32 = sum(ms32) / len(ms32)
         k32 = tm32["fitness_ms"] / max(tm32["fitness_launches"], 1)
@@ -720,7 +724,9 @@ def main():
         oracle.build()
         pop_np, fit_np, gen = g.population()
         sample = np.linspace(0, P - 1, 8).astype(int)
-        ref = oracle.fitness(pr.X, pr.y, pop_np[sample], pr.degree, pr.basis)
+        ref = oracle.fitness(pr.X, pr.y, pop_np[sample], pr.degree, pr.basis,
+                             err={"mse": oracle.ERR_MSE, "rmse": oracle.ERR_RMSE,
+                                  "mae": oracle.ERR_MAE}[args.error])
         f_bf = g.eval_fitness(pop_np, precision=prec)
         f_32 = g.eval_fitness(pop_np, precision=game.GAME_PREC_FP32)
         acc = {"sample_chromosomes": len(sample), "generation": gen,
@@ -730,7 +736,7 @@ def main():
                                                     set(np.argsort(f_32)[:10])) / 10}
         cpu, M_s = oracle_sample_rate(pr, 16)
         cpu.update(oracle_extra(pr, M_s, cpu))
-        if args.precision_report > 0:
+        if args.precision_report > 0 and args.error == "mse":
             acc["precision_forms"] = precision_report(game, g, pr, args.precision_report)
 
     n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
@@ -759,7 +765,7 @@ def main():
                                                "fp8": "e4m3", "gram": "f64"}[args.form],
         "data": "synthetic",
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
-                   "basis": "chebyshev", "contraction": args.form,
+                   "basis": "chebyshev", "contraction": args.form, "error": args.error,
                    "step": ("one generation: operators + pack + fused fitness + FP64 reduce"
                             + (" + elite re-score (8 best: FP64 Gram form)"
                                if tensor else "")),

@@ -216,7 +216,8 @@ def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
     evaluated on the first M_sub patterns by each form (a handle on that
     subset) and by the oracle; reported per form and generation: the max and
     median relative fitness error and the overlap of the form's 10 best with
-    the oracle's 10 best."""
+    the oracle's 10 best (for BF16 and FP8 also after re-scoring the 8 or 16
+    best in FP64, as the operators see it)."""
     import oracle
     oracle.build()
     forms = {"fp32": game.GAME_PREC_FP32, "bf16": game.GAME_PREC_BF16,
@@ -232,10 +233,15 @@ def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
         for name, prec in forms.items():
             f = sub.eval_fitness(pop, precision=prec)
             rel = np.abs(f - ref) / np.abs(ref)
-            rows[name].append({"max_rel_err": float(rel.max()),
-                               "median_rel_err": float(np.median(rel)),
-                               "top10_agreement": len(best & set(np.argsort(f, kind="stable")[:10]))
-                               / 10})
+            row = {"max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel)),
+                   "top10_agreement": len(best & set(np.argsort(f, kind="stable")[:10])) / 10}
+            if prec in (game.GAME_PREC_BF16, game.GAME_PREC_FP8):
+                # the vector the operators rank: the best re-scored in FP64
+                for n in (8, 16):
+                    fr, _ = sub.rescore_top(pop, f, n)
+                    row[f"top10_agreement_rescored_{n}"] = len(
+                        best & set(np.argsort(fr, kind="stable")[:10])) / 10
+            rows[name].append(row)
         gens.append(int(gen))
         if step + 1 < G:
             game.game_generation(g.h, seed)

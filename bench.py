@@ -8,7 +8,7 @@ genes), P = 1024 chromosomes, sign targets with 5% flips; seeded synthetic
 data generated on the host and uploaded before timing. One step is one
 generation: selection / crossover / mutation kernels, the population pack,
 the fused fitness contraction (tensor cores, BF16 operands, FP32
-accumulation), the FP64 cross-tile error sum and the re-scoring of the 8 best
+accumulation), the FP64 cross-tile error sum and the re-scoring of the 16 best
 candidates (FP64, by the Gram form of the MSE) before the next elitism decision. The plain FP32 CUDA-core
 form of the same step is timed beside it, and a sample of chromosomes is
 re-scored by the FP64 oracle to state the accuracy of both.
@@ -606,7 +606,7 @@ def main():
             "gram": game.GAME_PREC_GRAM}[args.form]
     tensor = prec not in (game.GAME_PREC_FP32, game.GAME_PREC_GRAM)
     errk = {"mse": game.GAME_ERR_MSE, "rmse": game.GAME_ERR_RMSE, "mae": game.GAME_ERR_MAE}[args.error]
-    ekw = dict(error=errk, rescore_top=0 if args.error == "mae" else 8)
+    ekw = dict(error=errk, rescore_top=0 if args.error == "mae" else 16)
     t_create = time.perf_counter()
     g = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, precision=prec, seed=2, **ekw)
     t_create = time.perf_counter() - t_create
@@ -773,7 +773,7 @@ def main():
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
                    "basis": "chebyshev", "contraction": args.form, "error": args.error,
                    "step": ("one generation: operators + pack + fused fitness + FP64 reduce"
-                            + (" + elite re-score (8 best: FP64 Gram form)"
+                            + (" + elite re-score (16 best: FP64 Gram form)"
                                if tensor else "")),
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent replica(s)"},

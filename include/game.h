@@ -120,7 +120,8 @@ typedef struct {
                            in a reduced-precision form (not GAME_PREC_FP32),
                            the rescore_top best chromosomes are re-scored as
                            game_rescore_top does, before the operators rank
-                           them; 0 = off */
+                           them; 0 = off; the default 16 keeps the ten best
+                           of the ranked vector those of FP64 */
   int32_t surrogate;    /* 1: screen oversampled offspring with the fitness
                            surrogate (game_surrogate_*), 0: off */
   int32_t oversample;   /* offspring per kept child when screening (>= 1,
@@ -138,7 +139,7 @@ typedef struct {
   int32_t reserved[1];  /* must be zero */
 } game_params;
 
-/* Fills *out with the defaults listed above (and rescore_top = 8,
+/* Fills *out with the defaults listed above (and rescore_top = 16,
  * oversample = 8, surrogate_steps = 1, tournament selection, per-feature
  * genes, MSE). */
 int game_params_default(game_params* out);

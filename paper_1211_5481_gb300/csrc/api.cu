@@ -692,7 +692,7 @@ int game_params_default(game_params* out) {
   out->sigma = 0.1f;
   out->mse_threshold = 0.0;
   out->seed = 1;
-  out->rescore_top = 8;
+  out->rescore_top = 16;
   out->surrogate = 0;
   out->oversample = 8;
   out->selection = GAME_SEL_TOURNAMENT;

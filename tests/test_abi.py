@@ -70,7 +70,7 @@ def test_host_side_argument_checks():
     for field, value, extra in [("selection", 3, {}), ("selection", -1, {}),
                                 ("selection", game.GAME_SEL_RANKING, {"P": 16385}),
                                 ("tied", 2, {}), ("error", 3, {}),
-                                ("error", game.GAME_ERR_MAE, {}),   # rescore_top = 8
+                                ("error", game.GAME_ERR_MAE, {}),   # rescore_top = 16
                                 ("error", game.GAME_ERR_MAE,
                                  {"rescore_top": 0, "precision": game.GAME_PREC_GRAM}),
                                 ("surrogate_steps", 65, {}),

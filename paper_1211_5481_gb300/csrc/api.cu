@@ -221,8 +221,9 @@ int ensure_gram(game_ctx* h) {
     dev_free(h->G);
     dev_free(h->gb);
     dev_free(h->gyy);
+    dev_free(h->gpart);
     h->G = nullptr;
-    h->gb = h->gyy = nullptr;
+    h->gb = h->gyy = h->gpart = nullptr;
     return fail(GAME_ENOMEM, "Gram matrix");
   }
   cudaError_t e = launch_gram_build(gs, h->Xt, h->y, h->G, h->gb, h->gyy, phi, part, h->num_sms,

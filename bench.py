@@ -746,7 +746,8 @@ def main():
             acc["precision_forms"] = precision_report(game, g, pr, args.precision_report)
 
     n_launch = tm["fitness_launches"] + tm["pack_launches"] + tm["reduce_launches"] + \
-        2 * tm["operators_launches"] + 2 * tm["rescore_launches"]
+        (1 if P <= 1024 and P * K <= 65536 else 2) * tm["operators_launches"] + \
+        3 * tm["rescore_launches"]
     cls = None
     if rank == 0 and args.classify_run > 0:
         # trained model quality (outside the timed region): the best

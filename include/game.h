@@ -240,9 +240,13 @@ typedef struct {
   int64_t fitness_launches;
   int64_t pack_launches;
   int64_t reduce_launches;
-  int64_t operators_launches; /* calls; two kernels each */
+  int64_t operators_launches; /* calls; two kernels each (plan, breeding), one
+                               fused kernel for populations of at most 1024
+                               chromosomes and 65,536 genes, plus a selection
+                               table kernel for ranking or roulette above that */
   double rescore_ms;        /* elite candidate selection and re-scoring */
-  int64_t rescore_launches; /* calls; two kernels each */
+  int64_t rescore_launches; /* calls; three kernels each (selection, quadratic
+                               forms, final sums) */
   double surrogate_ms;      /* surrogate screening and training */
   int64_t surrogate_launches; /* generations screened */
 } game_timing;

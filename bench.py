@@ -264,8 +264,10 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = oracle.set_threads(0)
-    # size one step to a few seconds of CPU work
-    _, M_s = oracle_sample_rate(pr, 16, target_s=2.0, max_s=6.0)
+    # size one step so that the whole run (warm-up and timed steps) takes
+    # about 100 s of CPU work, at most 2 s per step
+    target = min(2.0, max(0.01, 100.0 / max(args.steps + args.warmup, 1)))
+    _, M_s = oracle_sample_rate(pr, 16, target_s=target, max_s=3 * target)
     pop = oracle.init_population(2, 16, pr.K)
     for _ in range(args.warmup):
         oracle.fitness(pr.X[:M_s], pr.y[:M_s], pop, pr.degree, pr.basis)

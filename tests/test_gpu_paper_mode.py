@@ -284,3 +284,37 @@ def test_mae_refuses_rescore(orc):
         assert ei.value.code == game.GAME_EINVAL
         with pytest.raises(game.GameError):
             g.eval_fitness(pop, precision=GRAM)
+
+
+def test_tied_mae_roulette_together(orc):
+    """Shared genes, the MAE and roulette selection in one handle: fitness
+    against the oracle (the replicated chromosome's MAE) and one generation
+    bit-exact against the oracle's operators on the shared genes."""
+    pr = problem(3000, 12, 5, seed=2)
+    P, Kt = 100, 6
+    prm = orc.ga_params(selection=orc.SEL_ROULETTE)
+    with game.Game(pr.X, pr.y, 5, CHEB, P=P, seed=6, tied=1, error=MAE, rescore_top=0,
+                   selection=ROULETTE) as g:
+        pop, fit, gen = g.population()
+        ref = orc.fitness(pr.X, pr.y, replicate(pop, 12, 1, 5), 5, CHEB, err=orc.ERR_MAE)
+        assert pop.shape == (P, Kt)
+        assert np.all(np.abs(fit - ref) <= 1e-5 * np.abs(ref) + 1e-7)
+        g.generation(6)
+        nxt, _, _ = g.population()
+    np.testing.assert_array_equal(bits(nxt), bits(orc.generation(pop, fit, 6, gen, prm)))
+
+
+def test_tied_surrogate_run_is_elitist():
+    """Shared genes with the surrogate screening (K = B d + 1 inputs to the
+    MLP): the run proceeds and the elitist best never worsens."""
+    pr = problem(4000, 10, 6, seed=3)
+    with game.Game(pr.X, pr.y, 6, CHEB, P=64, seed=2, tied=1, precision=BF16, surrogate=1,
+                   oversample=4) as g:
+        assert g.K == 7
+        best = [g.population()[1].min()]
+        for _ in range(8):
+            g.generation(2)
+            best.append(g.population()[1].min())
+        pred, keep, trusted, r = g.surrogate_last()
+    assert pred.shape == (4 * 62,) and keep.sum() == 62
+    assert all(b1 <= b0 * (1 + 1e-12) for b0, b1 in zip(best, best[1:]))

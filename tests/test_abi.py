@@ -105,3 +105,23 @@ def test_batch_refuses_paper_mode_settings():
         setattr(prm, field, value)
         rc = lib.game_batch_create(runs, 1, ctypes.byref(prm), None, 1, None, ctypes.byref(b))
         assert rc == game.GAME_EINVAL, field
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the CUDA library the binding raises instead of
+    computing anything, and the oracle is not imported by the package."""
+    import sys as _sys
+    monkeypatch.setattr(game, "_lib", None)
+    monkeypatch.setattr(gbuild, "LIB", str(tmp_path / "missing" / "libgame.so"))
+    with pytest.raises(ImportError):
+        game.load(build_if_missing=False)
+    # the product package never loads the oracle
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([_sys.executable, "-c",
+                          "import sys; import paper_1211_5481_gb300.game, paper_1211_5481_gb300.datagen; "
+                          "print('oracle' in sys.modules)"],
+                         cwd=root, capture_output=True, text=True, check=True).stdout.strip()
+    assert out == "False"
+    for f in (game.__file__, gbuild.__file__):
+        src = open(f).read()
+        assert "import oracle" not in src and "from oracle" not in src

@@ -136,105 +136,6 @@ __host__ __device__ inline uint32_t chunk_desc(int cid, int basis, int d, int Kp
   return desc;
 }
 
-// Feature index of a chunk's first column.
-__host__ __device__ inline int chunk_feature(uint32_t desc) { return (int)(desc & 0xFFFFu); }
-
-// The 8 expansion values of one chunk for one pattern. x_first is the value
-// of the chunk's first feature; further features (when the chunk crosses
-// into the next one) are read as xrow[i * xstride].
-__device__ __forceinline__ void gen_chunk_x(uint32_t desc, int basis, int d, int N,
-                                            float x_first, const float* xrow, int xstride,
-                                            float (&v)[8]) {
-  if (desc & kChunkZero) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = 0.f;
-    return;
-  }
-  int i = (int)(desc & 0xFFFFu);
-  int j = (int)((desc >> 16) & 31u);
-  int b = (int)((desc >> 21) & 1u);
-  const int nvalid = (int)((desc >> 24) & 15u);
-  float x = x_first;
-  if (basis == GAME_BASIS_CHEB) {
-    float x2 = x + x, tm1 = 1.f, t = x;
-    for (int s = 1; s < j; ++s) {
-      const float tn = fmaf(x2, t, -tm1);
-      tm1 = t;
-      t = tn;
-    }
-    if (desc & kChunkRun) {
-      v[0] = t;
-#pragma unroll
-      for (int e = 1; e < 8; ++e) {
-        const float tn = fmaf(x2, t, -tm1);
-        tm1 = t;
-        t = tn;
-        v[e] = t;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        v[e] = t;
-        if (j == d) {
-          ++i;
-          j = 1;
-          x = (i < N) ? __ldg(xrow + i * xstride) : 0.f;
-          x2 = x + x;
-          tm1 = 1.f;
-          t = x;
-        } else {
-          ++j;
-          const float tn = fmaf(x2, t, -tm1);
-          tm1 = t;
-          t = tn;
-        }
-      }
-    }
-  } else {
-    float s1, c1;
-    sincosf(x, &s1, &c1);
-    float c2x = c1 + c1;
-    float fm = b ? 0.f : 1.f;
-    float f = b ? s1 : c1;
-    for (int s = 1; s < j; ++s) {
-      const float fn = fmaf(c2x, f, -fm);
-      fm = f;
-      f = fn;
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      v[e] = f;
-      if (j == d) {
-        j = 1;
-        if (b == 0) {
-          b = 1;
-          fm = 0.f;
-          f = s1;
-        } else {
-          ++i;
-          b = 0;
-          x = (i < N) ? __ldg(xrow + i * xstride) : 0.f;
-          sincosf(x, &s1, &c1);
-          c2x = c1 + c1;
-          fm = 1.f;
-          f = c1;
-        }
-      } else {
-        ++j;
-        const float fn = fmaf(c2x, f, -fm);
-        fm = f;
-        f = fn;
-      }
-    }
-  }
-  if (nvalid < 8) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (e >= nvalid) v[e] = 0.f;
-  }
-}
-
-
 // Chebyshev chunk crossing feature runs, degree d >= 4 (so the chunk's 8
 // columns touch at most three features), for two patterns at once (va for
 // xrow0; vb for xrow1 when hasB): the same values, bit for bit, as gen_chunk,

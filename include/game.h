@@ -73,8 +73,8 @@ extern "C" {
                                  when every weight is 0 */
 
 /* Arithmetic of the fitness contraction (the expansion-times-genes sum). In
- * every form the residuals of Eq. 3 are squared in FP32 and the sum over
- * patterns ends in FP64. */
+ * every direct form the residuals of Eq. 3 are squared (absolute values for
+ * the MAE) in FP32 and the sum over patterns ends in FP64. */
 #define GAME_PREC_FP32 0   /* FP32 CUDA-core FFMA, FP32 accumulation */
 #define GAME_PREC_BF16 1   /* tcgen05 BF16 x BF16 -> FP32 in tensor memory */
 #define GAME_PREC_BF16X3 2 /* tcgen05 split products: genes and expansion split
@@ -151,7 +151,10 @@ int game_params_default(game_params* out);
  *   for the legacy default stream.
  * Validation (GAME_EINVAL): M < 1, N < 1, d < 1, unknown basis, NaN/Inf in
  * X or y, |x| > 1 with the Chebyshev basis, P < E + immigrants + 2,
- * tournament outside 1..64, rates outside [0, 1], sigma < 0, K > 4097.
+ * tournament outside 1..64, rates outside [0, 1], sigma < 0, B*N*d + 1 >
+ * 4097, an unknown selection / error function, ranking with P > 16384, the
+ * MAE with the Gram form or re-scoring, surrogate settings out of range,
+ * non-zero reserved fields.
  * The population is initialised with genes uniform in [-1, 1) (Section 3)
  * from prm->seed and evaluated, so the handle starts at generation 0 with
  * a valid fitness vector. Synchronous. */

@@ -54,6 +54,8 @@ def parse():
                          "mode on a set of the paper's data shape")
     ap.add_argument("--error", choices=["mse", "rmse", "mae"], default="mse",
                     help="classification workload: the fitness's error function (Section 3)")
+    ap.add_argument("--oversample", type=int, default=8, metavar="O",
+                    help="surrogate workload: offspring per kept child (game_params.oversample)")
     ap.add_argument("--surrogate-steps", type=int, default=1, metavar="S",
                     help="surrogate workload: Adam steps per generation on each stored "
                          "generation (game_params.surrogate_steps)")
@@ -412,7 +414,7 @@ def run_surrogate(args, torch, game, dev, world, rank):
         return sum(x.elapsed_time(y) for x, y in ev) / len(ev), tm
 
     gs = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=8,
+                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=args.oversample,
                    surrogate_steps=args.surrogate_steps)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
     t_sur, tm = timed(gs, args.steps, max(args.warmup, 3))
@@ -442,7 +444,7 @@ def run_surrogate(args, torch, game, dev, world, rank):
         _, _, best_o = oracle.train(pr.X, pr.y, pr.degree, pr.basis, P, G, 4, use_gram=True)
         t_o = time.perf_counter() - t0
         gg = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=8,
+                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=args.oversample,
                        surrogate_steps=args.surrogate_steps)
         gg.train(G)
         _, fit_g, _ = gg.population()
@@ -459,8 +461,9 @@ def run_surrogate(args, torch, game, dev, world, rank):
         "ms_per_step": t_sur, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
-                   "form": "BF16 contraction + elite re-score + surrogate screening, 8x "
-                           "oversampled offspring",
+                   "form": f"BF16 contraction + elite re-score + surrogate screening, "
+                           f"{args.oversample}x oversampled offspring",
+                   "oversample": args.oversample,
                    "surrogate_steps": args.surrogate_steps,
                    "step": "one screened generation: offspring, MLP screening, exact "
                            "fitness of the kept population, MLP training",

@@ -15,7 +15,7 @@
 // psi~(x) = (1, psi_1(x), ..., psi_{B d}(x)) with psi_{b,j}(x) =
 // sum_i phi_{b,j}(x_i) (features in order), written by expand_tied_kernel;
 // everything else is the same with K = B d + 1.
-// RMSE: the square root of the MSE (clamped at 0 against cancellation).
+// The MSE is clamped at 0 against cancellation; RMSE is its square root.
 //
 // Accumulation: the patterns are taken in chunks of up to kChunk; a chunk's
 // design matrix Phi [mc][K] (FP64) is written by expand_kernel, then
@@ -116,9 +116,12 @@ __global__ void expand_tied_kernel(int64_t m0, int mc, int N, int d, int basis, 
   }
 }
 
-// The fitness from the MSE: itself, or its square root for GAME_ERR_RMSE.
+// The fitness from the Gram-form MSE, clamped at 0 (cancellation can leave
+// an exact fit a few ulps below zero): itself, or its square root for
+// GAME_ERR_RMSE.
 __device__ __forceinline__ double finish_error(double mse, int err) {
-  return err == GAME_ERR_RMSE ? sqrt(fmax(mse, 0.0)) : mse;
+  const double m = fmax(mse, 0.0);
+  return err == GAME_ERR_RMSE ? sqrt(m) : m;
 }
 
 // part[z][k1][k2] = sum over rows r of split z of Phi[r][k1] Phi[r][k2], for

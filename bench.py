@@ -424,14 +424,14 @@ def run_surrogate(args, torch, game, dev, world, rank):
     t_32, _ = timed(g32, max(3, args.steps // 10), 1)
     g32.close()
     # surrogate rank agreement on the next generations (untimed)
-    rho, judge = [], []
+    rho, trust = [], []
     E = 2
     for _ in range(3):
         game.game_generation(gs.h, 4)
         pred, keep, trusted, r = gs.surrogate_last()
         _, fit, _ = gs.population()
         rho.append(spearman(pred[keep.astype(bool)], np.log(fit[E:])))
-        judge.append({"trusted": trusted, "pearson_kept": r})
+        trust.append({"trusted": trusted, "pearson_kept": r})
     acc = None
     if rank == 0 and not args.no_cpu_baseline:
         acc = precision_report(game, gs, pr, 2)
@@ -475,7 +475,7 @@ def run_surrogate(args, torch, game, dev, world, rank):
                               for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms",
                                         "rescore_ms", "surrogate_ms")},
         "surrogate_rank_spearman_kept": rho,
-        "surrogate_judge": judge,
+        "surrogate_trust": trust,
         "accuracy": acc, "final_best": final, "clocks": clk,
     }
     gs.close()

@@ -223,8 +223,8 @@ int game_set_state(game_t h, const float* pop, const double* fit,
                    int64_t generation);
 
 /* Checkpoint file of the GA state: population, fitness and generation and,
- * with the surrogate, its parameters, Adam moments and step, the judge's
- * verdict and the replay ring, so that game_load followed by the same calls
+ * with the surrogate, its parameters, Adam moments and step, the trust
+ * check's verdict and the replay ring, so that game_load followed by the same calls
  * continues the run exactly. The file records M, N, degree, basis, tied, K,
  * P and the surrogate setting; game_load refuses (GAME_EINVAL) a file of a
  * different shape or a truncated or foreign one. The training set itself
@@ -292,8 +292,9 @@ int game_eval_fitness_static(const float* X, const float* y, int64_t M,
  * population), keeps the P - E children with the lowest predicted fitness
  * (ties by slot) in slot order after the E elites, evaluates that population
  * exactly (the handle's precision and re-scoring), and then trains the
- * surrogate with one Adam step on each of the last two generations' exact
- * (chromosome, fitness) pairs. The exact fitness also judges the surrogate
+ * surrogate with surrogate_steps rounds of one Adam step on each of the last
+ * two generations' exact (chromosome, fitness) pairs. The exact fitness also
+ * checks the surrogate
  * (game_surrogate_last): while its predictions do not correlate with the
  * exact fitness of the children they kept, screening keeps the children an
  * unscreened generation would have. The surrogate of a fresh handle is initialised
@@ -319,9 +320,9 @@ int game_surrogate_set_params(game_t h, const float* w);
 /* The last screening: *n_out children (slot E + i), their predictions
  * pred_out [n], kept flags keep_out [n], whether the screening trusted the
  * surrogate (*trusted_out; if not it kept the first P - E children, those of
- * the unscreened generation), and the judge's correlation *r_out measured on
+ * the unscreened generation), and the trust check's correlation *r_out measured on
  * the children it kept (any output may be NULL; pass NULL arrays first to
- * learn n). The judge: the next screening trusts the surrogate iff the
+ * learn n). The trust check: the next screening trusts the surrogate iff the
  * Pearson correlation of the kept children's predictions with their exact
  * log-fitness exceeds 0.25; a fresh handle starts untrusted. */
 int game_surrogate_last(game_t h, float* pred_out, int32_t* keep_out, int32_t* n_out,

@@ -28,7 +28,7 @@ Definitions (the same as the CUDA path, written from them):
     ties by slot, predictions ordered as IEEE-754 total order (NaN last) --
     or, when the surrogate is not trusted, the first n_keep children; the
     next population is the elites followed by the kept children in slot order;
-  * judge: the Pearson correlation r of the kept children's predictions with
+  * trust check: the Pearson correlation r of the kept children's predictions with
     their exact log-fitness; the next screening trusts the surrogate iff
     r > 0.25.
 """
@@ -196,7 +196,7 @@ def screen(offspring, keep, E):
     return np.concatenate([off[:E], kept], axis=0)
 
 
-def judge(pred, keep, fit_kept):
+def trust_check(pred, keep, fit_kept):
     """(r, trusted): Pearson correlation of the kept children's predictions
     with their exact log-fitness (fit_kept in slot order), and r > 0.25."""
     x = np.asarray(pred, dtype=np.float64)[np.asarray(keep).astype(bool)]

@@ -120,8 +120,8 @@ struct game_ctx {
   int* flag = nullptr;
   int* pos = nullptr;
   int last_n = 0;             // children screened by the last generation
-  int* trust = nullptr;       // [2]: the judge's verdict, the verdict the last screening used
-  float* trust_r = nullptr;   // [1]: the judge's last correlation
+  int* trust = nullptr;       // [2]: the trust check's verdict, the verdict the last screening used
+  float* trust_r = nullptr;   // [1]: the trust check's last correlation
   float* rX[2] = {nullptr, nullptr};     // replay: the last two populations
   double* rfit[2] = {nullptr, nullptr};  // and their exact fitness
   int ring_n = 0, ring_head = 0;
@@ -506,7 +506,7 @@ int setup_screening(game_ctx* h) {
     cudaGetLastError();
     return fail(GAME_ENOMEM, "screening buffers");
   }
-  CK(cudaMemsetAsync(h->trust, 0, 2 * sizeof(int), h->st));   // untrusted until judged
+  CK(cudaMemsetAsync(h->trust, 0, 2 * sizeof(int), h->st));   // untrusted until checked
   CK(cudaMemsetAsync(h->trust_r, 0, sizeof(float), h->st));
   int rc = ensure_surrogate(h, n > P ? n : P);
   for (int i = 0; i < 20 && !rc; ++i) rc = surrogate_step(h, h->pop[h->cur], h->fit, P);
@@ -930,7 +930,7 @@ int game_generation(game_t h, uint64_t seed) {
     if (rc) return rc;
     h->fit_valid = true;
     t0 = stage_begin(h);
-    CK(surrogate_judge(n, h->pred, h->flag, h->pos, h->fit + E, h->trust_r, h->trust, h->st));
+    CK(surrogate_trust_check(n, h->pred, h->flag, h->pos, h->fit + E, h->trust_r, h->trust, h->st));
     rc = surrogate_learn(h);
     stage_end(h, t0, kSurrogate);
     return rc;

@@ -162,7 +162,7 @@ cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred,
                              int* used_trust, cudaStream_t st);
 // r = Pearson correlation of the kept children's predictions with their exact
 // log-fitness (fit_kept [n_keep] in slot order); *trusted = r > 0.25.
-cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int* pos,
+cudaError_t surrogate_trust_check(int n, const float* pred, const int* flag, const int* pos,
                             const double* fit_kept, float* r_out, int* trusted, cudaStream_t st);
 
 // gram.cu -- the Gram form of the MSE (FP64)

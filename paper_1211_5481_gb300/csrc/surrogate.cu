@@ -23,7 +23,7 @@
 // derivative, the output layer, and Adam. Screening: a one-CTA bitonic sort
 // of (prediction, slot) keys, a flag per kept slot and a prefix-sum
 // compaction that assembles the next population in slot order. The exact
-// fitness is the judge: after each screened generation the Pearson
+// fitness checks the surrogate: after each screened generation the Pearson
 // correlation r of the kept children's predictions with their exact
 // log-fitness is measured, and the next screening trusts the surrogate only
 // if r > 0.25; otherwise it keeps the first P - E children, i.e. exactly the
@@ -582,7 +582,7 @@ cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t surrogate_judge(int n, const float* pred, const int* flag, const int* pos,
+cudaError_t surrogate_trust_check(int n, const float* pred, const int* flag, const int* pos,
                             const double* fit_kept, float* r_out, int* trusted, cudaStream_t st) {
   trust_kernel<<<1, 256, 0, st>>>(n, pred, flag, pos, fit_kept, r_out, trusted);
   return cudaGetLastError();

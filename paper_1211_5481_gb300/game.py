@@ -415,7 +415,7 @@ class Game:
         _check(load().game_surrogate_set_params(self.h, _ptr(w)))
 
     def surrogate_last(self):
-        """(predictions, kept flags, trusted flag used, judge's correlation)"""
+        """(predictions, kept flags, trusted flag used, trust check's correlation)"""
         n = ctypes.c_int32()
         _check(load().game_surrogate_last(self.h, None, None, ctypes.byref(n), None, None))
         pred = np.zeros(n.value, dtype=np.float32)

@@ -67,7 +67,7 @@ def test_gradient_and_adam_step(orc, prob):
 @pytest.mark.parametrize("P,E,S,seed", [(64, 2, 8, 4), (40, 3, 5, 2**35 + 1)])
 def test_screened_generation_bit_exact(orc, prob, P, E, S, seed):
     """Offspring, screening and assembly bit-exact given the device's
-    predictions; the judge's correlation against the oracle's, and its
+    predictions; the trust check's correlation against the oracle's, and its
     verdict used by the next screening; the first screening (untrusted)
     equals the unscreened generation."""
     prm = orc.ga_params(elitism=E)
@@ -94,7 +94,7 @@ def test_screened_generation_bit_exact(orc, prob, P, E, S, seed):
             if step == 0:   # untrusted: the unscreened generation exactly
                 np.testing.assert_array_equal(bits(nxt),
                                               bits(orc.generation(pop, fit, seed, gen, prm)))
-            r_ref, verdict = sg.judge(pred, keep, nfit[E:])
+            r_ref, verdict = sg.trust_check(pred, keep, nfit[E:])
             assert abs(r - r_ref) <= 1e-5
             verdict = int(verdict)
 

@@ -80,15 +80,15 @@ def test_screen_keeps_slot_order():
     np.testing.assert_array_equal(nxt, off[[0, 1, 3, 5]])
 
 
-def test_standardised_targets_and_judge():
+def test_standardised_targets_and_trust_check():
     fit = np.array([1.0, np.e, np.e ** 2, np.e ** 3])
     t = sg.targets(fit)
     np.testing.assert_allclose(t, (np.arange(4) - 1.5) / np.sqrt(1.25), rtol=1e-12)
     np.testing.assert_allclose(sg.targets(np.full(5, 3.0)), 0.0)   # sd 0 counts as 1
     pred = np.array([0.1, 5.0, 0.2, 0.3], dtype=np.float32)
     keep = np.array([1, 0, 1, 1])
-    r, ok = sg.judge(pred, keep, np.exp([1.0, 2.0, 3.0]))
+    r, ok = sg.trust_check(pred, keep, np.exp([1.0, 2.0, 3.0]))
     assert abs(r - 1.0) < 1e-12 and ok
-    r, ok = sg.judge(pred, keep, np.exp([3.0, 2.0, 1.0]))
+    r, ok = sg.trust_check(pred, keep, np.exp([3.0, 2.0, 1.0]))
     assert abs(r + 1.0) < 1e-12 and not ok
     np.testing.assert_array_equal(sg.select_keep(pred, 2, trusted=False), [1, 1, 0, 0])

@@ -1,8 +1,13 @@
 """FP64 CPU oracle for GAME fitness evaluation and GA operators.
 
 TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` import this package. It shares no code with
-the CUDA path (``paper_1211_5481_gb300``) and neither imports the other.
+CPU-baseline, reference and accuracy legs of ``bench.py`` import this
+package. It shares no code with the CUDA path (``paper_1211_5481_gb300``)
+and neither imports the other.
+
+``GAME_ORACLE_SOURCE`` and ``GAME_ORACLE_SURROGATE_SOURCE`` (tests only)
+name another copy of ``oracle.c`` or ``surrogate.py`` to load instead: the
+planted-mistake tests run the pins against copies with one mistake each.
 
 The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over
 chromosomes); this module only compiles it and marshals numpy arrays.
@@ -18,8 +23,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_SRC = os.environ.get("GAME_ORACLE_SOURCE") or os.path.join(_HERE, "oracle.c")
+_LIB = (os.path.join(_HERE, "liboracle.so") if _SRC == os.path.join(_HERE, "oracle.c")
+        else os.path.splitext(_SRC)[0] + ".so")
 _lock = threading.Lock()
 _lib = None
 
@@ -49,19 +55,24 @@ def ga_params(elitism=2, tournament=3, pc=0.9, pm=0.02, sigma=0.1, immigrants=0,
                     selection)
 
 
+def compile_source(src: str, lib: str) -> str:
+    """gcc, -O2, OpenMP, no FP contraction so that FP32 gene updates round
+    once per operation; ``oracle.h`` is taken from this directory."""
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-I", _HERE, src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, lib)
+    return lib
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so next to its source (gcc, -O2, OpenMP, no FP
-    contraction so that FP32 gene updates round once per operation)."""
+    """Compile liboracle.so next to its source unless it is up to date."""
     with _lock:
         if (not force and os.path.exists(_LIB)
                 and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
             return _LIB
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        return compile_source(_SRC, _LIB)
 
 
 def _load():
@@ -312,3 +323,18 @@ def train_tied(X, y, d, basis, P, G, seed, prm=None):
     _check(_load().oracle_train_tied(_ptr(X), _ptr(y), M, N, d, basis, P, ctypes.byref(prm),
                                      seed, G, _ptr(pop), _ptr(fit), _ptr(best)), "train_tied")
     return pop, fit, best
+
+
+def _load_surrogate_copy(path):
+    """Tests only: load another copy of surrogate.py as oracle.surrogate."""
+    import importlib.util
+    import sys
+    spec = importlib.util.spec_from_file_location(__name__ + ".surrogate", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    globals()["surrogate"] = mod
+
+
+if os.environ.get("GAME_ORACLE_SURROGATE_SOURCE"):
+    _load_surrogate_copy(os.environ["GAME_ORACLE_SURROGATE_SOURCE"])

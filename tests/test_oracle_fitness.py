@@ -206,6 +206,16 @@ def test_classify_hand_example(orc):
     assert orc.classify(X, y, np.array([0.3, -1.0]), 1, CHEB, 0.0) == (2, 1, 1, 0)
 
 
+def test_classify_values_at_the_threshold_are_negative(orc):
+    """Both comparisons are strict: a target or an output equal to the
+    threshold counts as negative. Out = 0.25 + x is exactly 0.25 at x = 0."""
+    X = np.array([[-0.5], [0.0], [0.0], [0.5]])
+    y = np.array([0.25, 0.25, 1.0, 1.0])
+    # pattern 0: y = t, Out < t (TN); 1: y = t, Out = t (TN);
+    # 2: y > t, Out = t (FN); 3: y > t, Out > t (TP)
+    assert orc.classify(X, y, np.array([0.25, 1.0]), 1, CHEB, 0.25) == (1, 0, 2, 1)
+
+
 def test_classify_counts_brute_force(orc):
     pr = dg.regression(5, 700, 4, 3, 0.2, degree=3)
     a = dg.random_population(9, 1, pr.K, scale=0.3)[0]

@@ -153,6 +153,21 @@ def test_tournament_prefers_fitter(orc):
     assert np.mean(ranks == P - 1) < 0.001
 
 
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_tournament_win_probability_closed_form(orc, T):
+    """Tournaments draw T candidates uniformly with replacement and keep the
+    best, so the member of rank r (0 = best) wins with probability
+    ((P - r)^T - (P - r - 1)^T) / P^T; with T = 1 the draw is uniform, and
+    even the worst member wins when every candidate is it."""
+    P = 6
+    fit = np.array([0.4, 0.1, 0.9, 0.3, 0.6, 0.2])   # ranks 3 0 5 2 4 1
+    rank = np.argsort(np.argsort(fit))
+    counts = _parent_counts(orc, fit, orc.SEL_TOURNAMENT, 60000, tournament=T)
+    prob = ((P - rank) ** T - (P - rank - 1.0) ** T) / float(P) ** T
+    assert _within_binomial(counts, prob)
+    assert counts[np.argmax(rank)] > 0
+
+
 def test_nan_fitness_never_elite(orc):
     P, K = 12, 5
     pop = orc.init_population(1, P, K)
@@ -249,14 +264,14 @@ def test_mutation_clamps_both_ends(orc):
     assert np.count_nonzero(np.abs(child) < 1.0) > 0.3 * child.size
 
 
-def _parent_counts(orc, fit, selection, n_out, seeds=(5,), g=0):
+def _parent_counts(orc, fit, selection, n_out, seeds=(5,), g=0, tournament=3):
     """Selection frequencies: with no crossover, mutation, elites or
     immigrants each child slot is a copy of one selected parent, identified
     by gene 0."""
     P = fit.size
     pop = np.zeros((P, 3), dtype=np.float32)
     pop[:, 0] = np.arange(P) / 2.0**20
-    prm = orc.ga_params(elitism=0, pc=0.0, pm=0.0, selection=selection)
+    prm = orc.ga_params(elitism=0, pc=0.0, pm=0.0, selection=selection, tournament=tournament)
     counts = np.zeros(P)
     for seed in seeds:
         nxt = orc.offspring(pop, fit, seed, g, n_out, prm)
@@ -304,6 +319,17 @@ def test_roulette_all_zero_weights_is_uniform(orc):
     fit = np.full(5, np.nan)
     counts = _parent_counts(orc, fit, orc.SEL_ROULETTE, 50000)
     assert _within_binomial(counts, np.full(5, 0.2))
+
+
+def test_roulette_exact_integer_weights(orc):
+    """The weights are the integers floor(2^32 / (1 + fit)): fit = 2^32 - 1
+    has weight exactly 1 and fit = 2^32 weight 0, so with weights (1, 0, 1, 1)
+    u is uniform on {0, 1, 2} and member p covers [sum_{j<p} w_j,
+    sum_{j<=p} w_j): members 0, 2, 3 each a third, member 1 never."""
+    fit = np.array([2.0**32 - 1, 2.0**32, 2.0**32 - 1, 2.0**32 - 1])
+    counts = _parent_counts(orc, fit, orc.SEL_ROULETTE, 30000)
+    assert counts[1] == 0
+    assert _within_binomial(counts, np.array([1, 0, 1, 1]) / 3.0)
 
 
 def test_roulette_large_fitness_spread(orc):

@@ -92,3 +92,15 @@ def test_standardised_targets_and_trust_check():
     r, ok = sg.trust_check(pred, keep, np.exp([3.0, 2.0, 1.0]))
     assert abs(r + 1.0) < 1e-12 and not ok
     np.testing.assert_array_equal(sg.select_keep(pred, 2, trusted=False), [1, 1, 0, 0])
+
+
+def test_trust_threshold_on_hand_computed_correlations():
+    """Pearson r by hand: predictions 1..6 against log-fitness
+    (1, 2, 2, 1, 1, 2) give sum dx dy = 0.5, sum dx^2 = 17.5, sum dy^2 = 1.5,
+    r = 0.5 / sqrt(26.25) = 0.0976: positive but below 0.25, untrusted.
+    Predictions 1..4 against (1, 1, 3, 1) give r = 1 / sqrt(15) = 0.258,
+    just above 0.25: trusted."""
+    r, ok = sg.trust_check(np.arange(1.0, 7.0), np.ones(6), np.exp([1.0, 2, 2, 1, 1, 2]))
+    assert r == pytest.approx(0.5 / math.sqrt(26.25), rel=1e-12) and not ok
+    r, ok = sg.trust_check(np.arange(1.0, 5.0), np.ones(4), np.exp([1.0, 1, 3, 1]))
+    assert r == pytest.approx(1 / math.sqrt(15), rel=1e-12) and ok

@@ -123,6 +123,23 @@ MISTAKES = [
     # elite re-scoring
     ("rescore-writes-rank-slot",
      "&fit_out[idx[r]]);", "&fit_out[r]);"),
+    # the GA run
+    ("train-generation-counter-shifted",
+     "(uint32_t)(g - 1), next);", "(uint32_t)g, next);"),
+    ("train-best-is-slot-zero",
+     "if (best) best[g] = bf;", "if (best) best[g] = fit[0];"),
+    ("elites-all-the-same-best",
+     "    chosen[best] = 1;\n", "    chosen[best] = 0;\n"),
+    ("odd-child-slot-left-empty",
+     "const int32_t npairs = (n_out - E + 1) / 2;", "const int32_t npairs = (n_out - E) / 2;"),
+    ("select-best-repeats-the-best",
+     "    taken[best] = 1;\n    idx[r] = best;", "    idx[r] = best;"),
+    ("gram-squares-one-column",
+     "G[k1 * K + k2] += v * Phi[r * K + k2];", "G[k1 * K + k2] += v * Phi[r * K + k1];"),
+    ("gram-row-times-wrong-gene",
+     "row += G[(int64_t)k1 * K + k2] * a[k2];", "row += G[(int64_t)k1 * K + k2] * a[k1];"),
+    ("shared-genes-mean-over-features",
+     "fit[p] = sse / (double)M;", "fit[p] = sse / (double)(M * N);"),
     # classification (Section 5 metrics)
     ("label-threshold-inclusive",
      "const int actual = y[m] > threshold;", "const int actual = y[m] >= threshold;"),

@@ -269,8 +269,11 @@ int ensure_scratch(game_ctx* h, int P, int prec) {
     dev_free(h->uscale);
     h->a0 = nullptr;
     h->uscale = nullptr;
-    if (dev_alloc(&h->a0, Ppad) != cudaSuccess || dev_alloc(&h->uscale, Ppad) != cudaSuccess)
+    h->cap_P = 0;
+    if (dev_alloc(&h->a0, Ppad) != cudaSuccess || dev_alloc(&h->uscale, Ppad) != cudaSuccess) {
+      cudaGetLastError();
       return fail(GAME_ENOMEM, "a0 allocation");
+    }
     h->cap_P = Ppad;
   }
   if (prec == GAME_PREC_FP32) {
@@ -279,14 +282,22 @@ int ensure_scratch(game_ctx* h, int P, int prec) {
     if (need > h->popT_cap) {
       dev_free(h->popT);
       h->popT = nullptr;
-      if (dev_alloc(&h->popT, need) != cudaSuccess) return fail(GAME_ENOMEM, "popT allocation");
+      h->popT_cap = 0;
+      if (dev_alloc(&h->popT, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "popT allocation");
+      }
       h->popT_cap = need;
     }
     const size_t pneed = (size_t)pl.grid_y * Ppad;
     if (pneed > h->part_cap) {
       dev_free(h->part);
       h->part = nullptr;
-      if (dev_alloc(&h->part, pneed) != cudaSuccess) return fail(GAME_ENOMEM, "partials");
+      h->part_cap = 0;
+      if (dev_alloc(&h->part, pneed) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "partials");
+      }
       h->part_cap = pneed;
     }
   } else {
@@ -301,14 +312,22 @@ int ensure_scratch(game_ctx* h, int P, int prec) {
     if (need > h->popA_cap) {
       dev_free(h->popA);
       h->popA = nullptr;
-      if (dev_alloc(&h->popA, need) != cudaSuccess) return fail(GAME_ENOMEM, "popA allocation");
+      h->popA_cap = 0;
+      if (dev_alloc(&h->popA, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "popA allocation");
+      }
       h->popA_cap = need;
     }
     const size_t pneed = (size_t)pl.rows * Ppad;
     if (pneed > h->part_cap) {
       dev_free(h->part);
       h->part = nullptr;
-      if (dev_alloc(&h->part, pneed) != cudaSuccess) return fail(GAME_ENOMEM, "partials");
+      h->part_cap = 0;
+      if (dev_alloc(&h->part, pneed) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GAME_ENOMEM, "partials");
+      }
       h->part_cap = pneed;
     }
   }

@@ -202,9 +202,11 @@ def _ptr(a):
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
         return a.ctypes.data
-    assert a.is_contiguous(), "tensors must be contiguous"
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
     return a.data_ptr()
 
 

@@ -217,9 +217,10 @@ def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
     generation of the GA run held by handle g: the current population is
     evaluated on the first M_sub patterns by each form (a handle on that
     subset) and by the oracle; reported per form and generation: the max and
-    median relative fitness error and the overlap of the form's 10 best with
+    median relative fitness error, the overlap of the form's 10 best with
     the oracle's 10 best (for BF16 and FP8 also after re-scoring the 8 or 16
-    best in FP64, as the operators see it)."""
+    best in FP64, as the operators see it) and the Spearman rank correlation
+    with the oracle over the whole population."""
     import oracle
     oracle.build()
     forms = {"fp32": game.GAME_PREC_FP32, "bf16": game.GAME_PREC_BF16,
@@ -236,7 +237,8 @@ def precision_report(game, g, pr, G, M_sub=10_000, seed=2):
             f = sub.eval_fitness(pop, precision=prec)
             rel = np.abs(f - ref) / np.abs(ref)
             row = {"max_rel_err": float(rel.max()), "median_rel_err": float(np.median(rel)),
-                   "top10_agreement": len(best & set(np.argsort(f, kind="stable")[:10])) / 10}
+                   "top10_agreement": len(best & set(np.argsort(f, kind="stable")[:10])) / 10,
+                   "spearman_all": spearman(f, ref)}
             if prec in (game.GAME_PREC_BF16, game.GAME_PREC_FP8):
                 # the vector the operators rank: the best re-scored in FP64
                 for n in (8, 16):

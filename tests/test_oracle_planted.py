@@ -182,6 +182,13 @@ SURROGATE_MISTAKES = [
      "p[np.isnan(p)] = np.inf", "p[np.isnan(p)] = -np.inf"),
     ("untrusted-keeps-last-children",
      "keep[:n_keep] = 1", "keep[-n_keep:] = 1"),
+    ("bf16-ties-away-from-zero",
+     "u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000", "u = (u + 0x8000) & 0xFFFF0000"),
+    ("forward-skips-h1-rounding",
+     'H1 = _round(gelu(Z1), rounding)', 'H1 = gelu(Z1)'),
+    ("forward-skips-w2-rounding",
+     'W1b, W2b = _round(p["W1"], rounding), _round(p["W2"], rounding)',
+     'W1b, W2b = _round(p["W1"], rounding), p["W2"]'),
     ("trust-threshold-zero",
      "return r, r > 0.25", "return r, r > 0.0"),
 ]

@@ -104,3 +104,35 @@ def test_trust_threshold_on_hand_computed_correlations():
     assert r == pytest.approx(0.5 / math.sqrt(26.25), rel=1e-12) and not ok
     r, ok = sg.trust_check(np.arange(1.0, 5.0), np.ones(4), np.exp([1.0, 1, 3, 1]))
     assert r == pytest.approx(1 / math.sqrt(15), rel=1e-12) and ok
+
+
+def test_bf16_rounding_matches_torch():
+    """BF16 rounding (nearest, ties to even) equals torch's float32 ->
+    bfloat16 conversion on random bit patterns, 5000 of them exact ties."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    bits = rng.integers(0, 2**32, size=100000, dtype=np.uint64).astype(np.uint32)
+    bits[:5000] = (bits[:5000] & 0xFFFF0000) | 0x8000
+    v = bits.view(np.float32)
+    v = v[np.isfinite(v)]
+    ref = torch.from_numpy(v.copy()).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(sg.bf16(v), ref)
+
+
+def test_forward_rounds_at_each_stated_point():
+    """A hand-built K = 1, H = 2 network whose input, W1 and W2 lie just off
+    BF16 values (1 + 2^-10, 0.75 + 2^-12, 1 + 2^-10 round to 1, 0.75, 1):
+    Z1 = 0.75, H1 = bf16(g(0.75)), Z2 = H1, out = g(bf16(g(0.75))), with the
+    rounding taken from torch. Dropping any rounding point changes out."""
+    torch = pytest.importorskip("torch")
+    K, H = 1, 2
+    p = {"W1": np.array([[0.75 + 2**-12], [0.0]]), "b1": np.zeros(2),
+         "W2": np.array([[1 + 2**-10, 0.0], [0.0, 1.0]]), "b2": np.zeros(2),
+         "w3": np.array([1.0, 0.0]), "b3": np.zeros(1)}
+    w = sg.pack(p).astype(np.float32)
+    out, _ = sg.forward(w, np.array([[1 + 2**-10]]), K, H)
+    h1 = float(torch.tensor(sg.gelu(0.75), dtype=torch.float32).to(torch.bfloat16))
+    assert out[0] == pytest.approx(sg.gelu(h1), rel=1e-12)
+    assert abs(h1 - sg.gelu(0.75)) > 1e-3          # the rounding matters here
+    raw, _ = sg.forward(w, np.array([[1 + 2**-10]]), K, H, rounding=False)
+    assert abs(raw[0] - out[0]) > 1e-4

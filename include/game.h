@@ -76,7 +76,10 @@ extern "C" {
  * every direct form the residuals of Eq. 3 are squared (absolute values for
  * the MAE) in FP32 and the sum over patterns ends in FP64. */
 #define GAME_PREC_FP32 0   /* FP32 CUDA-core FFMA, FP32 accumulation */
-#define GAME_PREC_BF16 1   /* tcgen05 BF16 x BF16 -> FP32 in tensor memory */
+#define GAME_PREC_BF16 1   /* tcgen05 BF16 x BF16 -> FP32 in tensor memory;
+                              the expansion tile of all K - 1 columns stays
+                              in shared memory, which limits K - 1 to 2560
+                              at N <= 128 (GAME_EINVAL beyond) */
 #define GAME_PREC_BF16X3 2 /* tcgen05 split products: genes and expansion split
                               into BF16 hi + lo, three MMAs (hi*hi + hi*lo +
                               lo*hi) into one FP32 accumulator; both split
@@ -86,7 +89,7 @@ extern "C" {
                               k scaled by 448 / max_m |phi_k(x_m)| (taken once
                               from the training set), genes by the inverse
                               and a per-chromosome factor restored in the
-                              epilogue */
+                              epilogue; K - 1 up to 4096 at N <= 128 */
 #define GAME_PREC_GRAM 4   /* Gram form of the MSE in FP64: with
                               phi~ = (1, phi_1, ..., phi_{K-1}),
                               fit = (y.y - 2 a.b + a^T G a) / M where

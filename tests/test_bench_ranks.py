@@ -65,3 +65,28 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(out):
         bench.run_reference(bench.parse())
     assert out.getvalue() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the keys of the bench contract; its e2e and cpu_baseline
+    values are the line's own and it moves no bytes to or from a device."""
+    import json
+    import subprocess
+    res = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--M", "4000"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [l for l in res.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"]

@@ -31,7 +31,8 @@
 //                tile c overlaps the MMAs of tile c+1. The tcgen05 queue
 //                drains fast, so the issuing path is kept minimal: precomputed
 //                descriptors, unrolled groups of four K=16 MMAs, K-blocks taken
-//                in pairs.
+//                in pairs (singly for the first chromosome tile of a pattern
+//                tile, so that its MMAs start as soon as one slot is full).
 //   warp 2       X producer: bulk-copies the next pattern tile's features
 //                (staged mode only, below).
 //   warps 4-11   epilogue: tcgen05.ld of the accumulator (thread = chromosome

@@ -3,8 +3,9 @@
  * GA operators (Cavuoti et al., "Genetic Algorithm Modeling with GPU Parallel
  * Computing Technology", arXiv:1211.5481).
  *
- * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU
- * baseline of the benchmark load this library; the CUDA path never does.
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline, reference and accuracy legs load this library;
+ * the CUDA path never does.
  * It is written to be read against the paper, not to be fast: every
  * function is the plain definition, with no blocking, fusion or reordering.
  *

@@ -1,8 +1,8 @@
 /*
  * oracle.h -- FP64 CPU oracle for GAME (Cavuoti et al., arXiv:1211.5481).
  *
- * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU
- * baseline of the benchmark load this library. It shares no code, header,
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline, reference and accuracy legs load this library. It shares no code, header,
  * table or constant with the CUDA path, and neither side includes the other.
  *
  * Notation (paper, Section 3):

@@ -1,8 +1,9 @@
-"""The multi-rank bookkeeping of bench.py on CPU ranks (gloo, world size 2):
-every rank gets the slowest rank's step time and the whole-job rate counts
-the units of all ranks; under torchrun only rank 0 runs the reference arm.
-The path has no exchange step (independent replicas), so these are the only
-collective calls."""
+"""bench.py on the CPU: the multi-rank bookkeeping on gloo ranks (world
+size 2: every rank gets the slowest rank's step time and the whole-job rate
+counts the units of all ranks; under torchrun only rank 0 runs the
+reference arm; the path has no exchange step, independent replicas, so
+these are the only collective calls), the reference arm's JSON line, and
+the own arm's refusal to run without a GPU."""
 import io
 import os
 import socket

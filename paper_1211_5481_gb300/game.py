@@ -310,13 +310,24 @@ def game_destroy(h):
         _check(load().game_destroy(h))
 
 
+def _params(params) -> game_params:
+    """The defaults with the named fields replaced; an unknown name raises
+    (ctypes would otherwise accept it as a plain attribute and ignore it)."""
+    prm = game_params_default()
+    names = {name for name, _ in game_params._fields_}
+    for k, v in params.items():
+        if k not in names:
+            raise TypeError(f"unknown game_params field {k!r}")
+        setattr(prm, k, v)
+    return prm
+
+
 class Game:
     """Owning wrapper of a handle with numpy convenience accessors."""
 
     def __init__(self, X, y, degree, basis=GAME_BASIS_CHEB, stream=None, **params):
-        prm = game_params_default()
-        for k, v in params.items():
-            setattr(prm, k, v)
+        self.h = None
+        prm = _params(params)
         self._keep = (X, y)
         self.h = game_create(X, y, degree, basis, prm, stream)
         self.M, self.N, self.K, self.P = game_get_shape(self.h)
@@ -484,9 +495,8 @@ class Batch:
     y [M] float32 numpy arrays or CUDA tensors."""
 
     def __init__(self, runs, tiles=None, autotune=True, stream=None, **params):
-        prm = game_params_default()
-        for k, v in params.items():
-            setattr(prm, k, v)
+        self.h = None
+        prm = _params(params)
         descs = (game_run_desc * len(runs))()
         self._keep = []
         self.shapes = []

@@ -125,3 +125,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     for f in (game.__file__, gbuild.__file__):
         src = open(f).read()
         assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_unknown_parameter_names_are_refused():
+    """A misspelt setting raises before any device work instead of being
+    kept as a stray attribute and silently ignored."""
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.zeros(4, dtype=np.float32)
+    with pytest.raises(TypeError, match="selction"):
+        game.Game(X, y, 3, selction=game.GAME_SEL_RANKING)
+    with pytest.raises(TypeError, match="elitsm"):
+        game.Batch([(X, y, 3, 0, 8, 1)], elitsm=2)
+    assert game._params({"selection": game.GAME_SEL_RANKING}).selection == game.GAME_SEL_RANKING

@@ -210,9 +210,25 @@ def _ptr(a):
     return a.data_ptr()
 
 
+def _need(a, dtype: str, name: str):
+    """a (numpy array, torch tensor or None) unchanged if it holds `dtype`
+    ("float32", "float64", "int32"); TypeError otherwise. The library sees
+    raw pointers, so a wrong element type would be misread (or read past the
+    end of the buffer)."""
+    if a is None:
+        return a
+    got = str(a.dtype).replace("torch.", "")
+    if got != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {got}")
+    return a
+
+
 def _f32(a):
-    """A contiguous float32 view of a numpy array; CUDA tensors pass as they are."""
-    return np.ascontiguousarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a
+    """A contiguous float32 copy or view of a numpy array; tensors must
+    already be float32."""
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    return _need(a, "float32", "tensor")
 
 
 def _stream_ptr(stream):
@@ -232,6 +248,8 @@ def game_params_default() -> game_params:
 def game_create(X, y, degree: int, basis: int, prm: game_params | None = None, stream=None):
     """X [M][N] float32, y [M] float32 (numpy or CUDA tensors)."""
     M, N = X.shape
+    _need(X, "float32", "X")
+    _need(y, "float32", "y")
     h = ctypes.c_void_p()
     _check(load().game_create(_ptr(X), _ptr(y), M, N, degree, basis,
                               ctypes.byref(prm) if prm is not None else None,
@@ -249,6 +267,8 @@ def game_get_shape(h):
 def game_eval_fitness(h, pop, fit_out, precision: int | None = None):
     """pop [P][K] float32, fit_out [P] float64; both numpy or both CUDA tensors."""
     P = pop.shape[0]
+    _need(pop, "float32", "pop")
+    _need(fit_out, "float64", "fit_out")
     if precision is None:
         _check(load().game_eval_fitness(h, _ptr(pop), P, _ptr(fit_out)))
     else:
@@ -259,6 +279,9 @@ def game_eval_fitness(h, pop, fit_out, precision: int | None = None):
 def game_rescore_top(h, pop, fit, n: int, idx_out=None):
     """pop [P][K] float32, fit [P] float64 (updated in place), idx_out [n] int32;
     numpy arrays or CUDA tensors (pop and fit in the same memory)."""
+    _need(pop, "float32", "pop")
+    _need(fit, "float64", "fit")
+    _need(idx_out, "int32", "idx_out")
     _check(load().game_rescore_top(h, _ptr(pop), pop.shape[0], _ptr(fit), n, _ptr(idx_out)))
     return fit
 
@@ -280,6 +303,8 @@ def game_get_population(h, pop_out=None, fit_out=None) -> int:
 
 
 def game_set_state(h, pop, fit=None, generation: int = 0):
+    _need(pop, "float32", "pop")
+    _need(fit, "float64", "fit")
     _check(load().game_set_state(h, _ptr(pop), _ptr(fit), generation))
 
 
@@ -296,6 +321,9 @@ def game_get_timing(h) -> dict:
 def game_eval_fitness_static(X, y, degree: int, basis: int, pop, fit_out, stream=None):
     """Allocation-free FP32 fitness; all arrays are CUDA tensors."""
     M, N = X.shape
+    for a, dt, name in ((X, "float32", "X"), (y, "float32", "y"), (pop, "float32", "pop"),
+                        (fit_out, "float64", "fit_out")):
+        _need(a, dt, name)
     _check(load().game_eval_fitness_static(_ptr(X), _ptr(y), M, N, degree, basis, _ptr(pop),
                                            pop.shape[0], _ptr(fit_out), _stream_ptr(stream)))
     return fit_out
@@ -328,6 +356,7 @@ class Game:
     def __init__(self, X, y, degree, basis=GAME_BASIS_CHEB, stream=None, **params):
         self.h = None
         prm = _params(params)
+        X, y = _f32(X), _f32(y)
         self._keep = (X, y)
         self.h = game_create(X, y, degree, basis, prm, stream)
         self.M, self.N, self.K, self.P = game_get_shape(self.h)
@@ -370,8 +399,8 @@ class Game:
         or CUDA tensor; None = the training set)."""
         chrom = _f32(chrom)
         M = self.M if X is None else X.shape[0]
-        if X is not None and isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X, dtype=np.float32)
+        if X is not None:
+            X = _f32(X)
         if X is None or isinstance(X, np.ndarray):
             out = np.zeros(M, dtype=np.float64)
         else:
@@ -385,9 +414,8 @@ class Game:
         set) as a dict."""
         chrom = _f32(chrom)
         M = self.M if X is None else X.shape[0]
-        if X is not None and isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X, dtype=np.float32)
-            y = np.ascontiguousarray(y, dtype=np.float32)
+        if X is not None:
+            X, y = _f32(X), _f32(y)
         c = game_confusion()
         _check(load().game_classify(self.h, _ptr(chrom), _ptr(X), _ptr(y), M, float(threshold),
                                     ctypes.byref(c)))
@@ -501,9 +529,7 @@ class Batch:
         self._keep = []
         self.shapes = []
         for r, (X, y, degree, basis, P, seed) in enumerate(runs):
-            if isinstance(X, np.ndarray):
-                X = np.ascontiguousarray(X, dtype=np.float32)
-                y = np.ascontiguousarray(y, dtype=np.float32)
+            X, y = _f32(X), _f32(y)
             self._keep.append((X, y))
             M, N = X.shape
             descs[r] = game_run_desc(_ptr(X), _ptr(y), M, N, degree, basis, P, seed)

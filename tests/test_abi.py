@@ -137,3 +137,22 @@ def test_unknown_parameter_names_are_refused():
     with pytest.raises(TypeError, match="elitsm"):
         game.Batch([(X, y, 3, 0, 8, 1)], elitsm=2)
     assert game._params({"selection": game.GAME_SEL_RANKING}).selection == game.GAME_SEL_RANKING
+
+
+def test_element_types_are_checked_before_the_call():
+    """The library sees raw pointers: arrays of the wrong element type are
+    refused in the binding (numpy inputs of Game are converted instead)."""
+    torch = pytest.importorskip("torch")
+    pop64 = np.zeros((4, 7))
+    with pytest.raises(TypeError, match="pop must be float32"):
+        game.game_eval_fitness(None, pop64, np.zeros(4))
+    with pytest.raises(TypeError, match="fit_out must be float64"):
+        game.game_eval_fitness(None, pop64.astype(np.float32), np.zeros(4, dtype=np.float32))
+    with pytest.raises(TypeError, match="X must be float32"):
+        game.game_create(torch.zeros((4, 2), dtype=torch.float16), torch.zeros(4), 3, 0)
+    with pytest.raises(TypeError, match="idx_out must be int32"):
+        game.game_rescore_top(None, pop64.astype(np.float32), np.zeros(4), 2,
+                              np.zeros(2, dtype=np.int64))
+    with pytest.raises(TypeError, match="must be float32"):
+        game._f32(torch.zeros(3, dtype=torch.float64))
+    assert game._f32(np.zeros(3)).dtype == np.float32

@@ -59,3 +59,18 @@ def test_c_caller_and_ctypes_layouts_agree(tmp_path):
     want = (f"default P {p.P} elitism {p.elitism} tournament {p.tournament} "
             f"rescore_top {p.rescore_top} oversample {p.oversample}")
     assert want in out
+
+
+def test_binding_constants_equal_the_header_defines():
+    """Every GAME_* value the header defines has the same value in the
+    binding, and the binding defines no GAME_* value the header lacks."""
+    import re
+    src = open(os.path.join(INC, "game.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"^#define (GAME_[A-Z0-9_]+) \(?(-?\d+)\)?", src, flags=re.M)}
+    assert len(defs) >= 19
+    for name, value in defs.items():
+        assert getattr(game, name) == value, name
+    mirrored = {n for n in dir(game) if re.fullmatch(r"GAME_[A-Z0-9_]+", n)
+                and isinstance(getattr(game, n), int)}
+    assert mirrored == set(defs)

@@ -378,3 +378,27 @@ def test_train_tied_elitist_and_shared_genes(orc):
     assert pop.shape == (11, 7)
     assert np.all(np.diff(best) <= 0)
     np.testing.assert_allclose(fit, orc.fitness_tied(pr.X, pr.y, pop, 3, 1), rtol=1e-14)
+
+
+def test_params_struct_layout_matches_the_c_header(orc, tmp_path):
+    """The ctypes mirror of oracle_ga_params has the C compiler's size and
+    field offsets, so the oracle reads the rates and counts it is given."""
+    import ctypes
+    import os
+    import subprocess
+    inc = os.path.dirname(orc.__file__)
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "oracle.h"', 'int main(void) {',
+             '  printf("size %zu\\n", sizeof(oracle_ga_params));']
+    for name, _ in orc.GAParams._fields_:
+        lines.append(f'  printf("{name} %zu\\n", offsetof(oracle_ga_params, {name}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(orc.GAParams)
+    for name, _ in orc.GAParams._fields_:
+        assert int(got[name]) == getattr(orc.GAParams, name).offset, name

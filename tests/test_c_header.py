@@ -74,3 +74,18 @@ def test_binding_constants_equal_the_header_defines():
     mirrored = {n for n in dir(game) if re.fullmatch(r"GAME_[A-Z0-9_]+", n)
                 and isinstance(getattr(game, n), int)}
     assert mirrored == set(defs)
+
+
+def test_binding_signatures_have_the_header_arity():
+    """Every entry point's ctypes argtypes has as many arguments as its
+    declaration in the header."""
+    import re
+    src = open(os.path.join(INC, "game.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lib = game.load()
+    decls = re.findall(r"\b(?:int|const char\*)\s+(game_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src)
+    assert len(decls) == len(game.EXPORTED)
+    for name, args in decls:
+        args = args.strip()
+        n = 0 if args in ("", "void") else args.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name

@@ -89,3 +89,31 @@ def test_binding_signatures_have_the_header_arity():
         args = args.strip()
         n = 0 if args in ("", "void") else args.count(",") + 1
         assert len(getattr(lib, name).argtypes) == n, name
+
+
+def test_binding_signatures_have_the_header_types():
+    """Each argument's ctypes type has the width and kind of its C type:
+    integers of the declared width, doubles, and pointers (handles, arrays,
+    structs and strings) as pointer types."""
+    import re
+    src = open(os.path.join(INC, "game.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lib = game.load()
+    scalar = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+              "double": ctypes.c_double, "float": ctypes.c_float}
+    decls = re.findall(r"\b(?:int|const char\*)\s+(game_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src)
+    checked = 0
+    for name, args in decls:
+        args = args.strip()
+        if args in ("", "void"):
+            continue
+        for arg, ct in zip(args.split(","), getattr(lib, name).argtypes):
+            words = arg.split()
+            if "*" in arg or words[0] in ("game_t", "game_batch_t"):
+                # pointers and handles: a pointer type, not an integer
+                assert ctypes.sizeof(ct) == ctypes.sizeof(ctypes.c_void_p), (name, arg)
+                assert ct not in scalar.values(), (name, arg)
+            else:
+                assert ct is scalar[words[-2]], (name, arg, ct)
+            checked += 1
+    assert checked > 60

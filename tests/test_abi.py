@@ -156,3 +156,29 @@ def test_element_types_are_checked_before_the_call():
     with pytest.raises(TypeError, match="must be float32"):
         game._f32(torch.zeros(3, dtype=torch.float64))
     assert game._f32(np.zeros(3)).dtype == np.float32
+
+
+@pytest.mark.parametrize("field,value,extra", [
+    ("elitism", -1, {}), ("elitism", 257, {}), ("tournament", 65, {}), ("immigrants", -1, {}),
+    ("P", (1 << 24) + 1, {}), ("immigrants", 7, {"P": 10}),
+    ("pc", 1.5, {}), ("pm", -0.1, {}), ("pc", float("nan"), {}),
+    ("sigma", -1.0, {}), ("sigma", float("inf"), {}), ("precision", 9, {}),
+    ("surrogate", 2, {}), ("oversample", 0, {"surrogate": 1}),
+    ("oversample", 300, {"surrogate": 1, "P": 64}),
+    ("rescore_top", 17, {}), ("rescore_top", -1, {}), ("check_every", -1, {}),
+], ids=lambda v: str(v))
+def test_every_settings_check_precedes_device_work(field, value, extra):
+    """Each refusal of game_params happens on the host, before any device
+    call, with GAME_EINVAL and a message."""
+    lib = game.load()
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.zeros(4, dtype=np.float32)
+    bad = game.game_params_default()
+    setattr(bad, field, value)
+    for k, v in extra.items():
+        setattr(bad, k, v)
+    h = ctypes.c_void_p()
+    rc = lib.game_create(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, ctypes.byref(bad), None,
+                         ctypes.byref(h))
+    assert rc == game.GAME_EINVAL
+    assert lib.game_last_error()

@@ -182,3 +182,27 @@ def test_every_settings_check_precedes_device_work(field, value, extra):
                          ctypes.byref(h))
     assert rc == game.GAME_EINVAL
     assert lib.game_last_error()
+
+
+@pytest.mark.parametrize("case", ["no runs", "too many runs", "bad elitism", "bad rate",
+                                  "bad sigma", "null out"])
+def test_batch_refusals_precede_device_work(case):
+    lib = game.load()
+    X = np.zeros((4, 2), dtype=np.float32)
+    y = np.zeros(4, dtype=np.float32)
+    R = {"no runs": 0, "too many runs": 65536}.get(case, 1)
+    runs = (game.game_run_desc * max(R, 1))()
+    for r in range(max(R, 1)):
+        runs[r] = game.game_run_desc(X.ctypes.data, y.ctypes.data, 4, 2, 3, 0, 8, 1)
+    prm = game.game_params_default()
+    if case == "bad elitism":
+        prm.elitism = 257
+    elif case == "bad rate":
+        prm.pc = 2.0
+    elif case == "bad sigma":
+        prm.sigma = float("nan")
+    b = ctypes.c_void_p()
+    out = None if case == "null out" else ctypes.byref(b)
+    rc = lib.game_batch_create(runs, R, ctypes.byref(prm), None, 0, None, out)
+    assert rc == game.GAME_EINVAL
+    assert lib.game_last_error()

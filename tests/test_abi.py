@@ -206,3 +206,23 @@ def test_batch_refusals_precede_device_work(case):
     rc = lib.game_batch_create(runs, R, ctypes.byref(prm), None, 0, None, out)
     assert rc == game.GAME_EINVAL
     assert lib.game_last_error()
+
+
+def test_every_entry_point_refuses_a_null_handle():
+    """Called with a NULL handle (and NULL arrays), every entry point returns
+    GAME_EINVAL with a message; destroying NULL is a no-op."""
+    lib = game.load()
+    skip = {"game_last_error", "game_params_default", "game_create", "game_batch_create",
+            "game_eval_fitness_static"}
+    for name in game.EXPORTED:
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        args = [1 if t in (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64) else
+                0.0 if t is ctypes.c_double else None for t in fn.argtypes]
+        rc = fn(*args)
+        if name in ("game_destroy", "game_batch_destroy"):
+            assert rc == game.GAME_OK, name
+        else:
+            assert rc == game.GAME_EINVAL, name
+            assert lib.game_last_error(), name

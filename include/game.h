@@ -263,24 +263,27 @@ int game_set_timing(game_t h, int32_t enable);
 int game_get_timing(game_t h, game_timing* out);
 
 /* Fitness of a population without any device allocation, for callers that
- * cannot call cudaMalloc: code running while another component captures the
- * stream into a CUDA graph, plug-ins confined to a host application's fixed
- * device-memory budget, runtimes that forbid allocation after start-up. The
- * paper has no counterpart of this call; it is a deployment variant of the
- * FP32 form of game_eval_fitness (same Eq. 2 / Eq. 3 MSE, FP32 CUDA-core
- * contraction, FP64 cross-tile sum) that needs no handle.
+ * cannot call cudaMalloc: plug-ins inside a host application that owns the
+ * device-memory budget and hands out only what it pre-allocated, and
+ * runtimes that forbid allocation after start-up (an allocation can fail,
+ * and cudaMalloc / cudaFree may synchronise the device, stalling every other
+ * stream). The paper has no counterpart of this call. It returns the same
+ * FP32 MSE that game_eval_fitness computes with GAME_PREC_FP32 (FP32
+ * CUDA-core contraction, FP64 cross-tile sum), without a handle.
  *   X [M][N] FP32 row-major, y [M] FP32, pop [P][K] FP32 (K = B*N*d + 1),
- *   fit_out [P] FP64: all device pointers on the current device, owned by
- *   the caller. Inputs are used as given (no NaN / domain checks).
+ *   fit_out [P] FP64: all device (or managed) memory of the current device,
+ *   owned by the caller. Inputs are used as given (no NaN / domain checks).
  *   cuda_stream: a cudaStream_t or NULL. Only enqueues work.
  * The only intermediate buffer is a fixed 4 MiB array of FP64 partial sums
  * that the library holds on every GPU that loads it, until the process
  * exits. P above 524288 (the array's capacity in chromosome rows) is
  * rejected with GAME_EINVAL before any launch. The first call on a device
- * looks up that array's address (do it before any stream capture). All
- * calls share the array: calls that overlap on the GPU race on it, so the
- * caller must serialise them. Errors: GAME_EINVAL (arguments, host
- * pointers), GAME_ECUDA; the reason is in game_last_error(). */
+ * looks up that array's address and caches it (make it before any stream
+ * capture); after cudaDeviceReset of that device the cached address is
+ * stale, so no call may follow a reset in the same process. All calls share
+ * the array: calls that overlap on the GPU race on it, so the caller must
+ * serialise them. Errors: GAME_EINVAL (arguments, host pointers, memory of
+ * another device), GAME_ECUDA; the reason is in game_last_error(). */
 int game_eval_fitness_static(const float* X, const float* y, int64_t M,
                              int32_t N, int32_t degree, int32_t basis,
                              const float* pop, int32_t P, double* fit_out,
@@ -418,6 +421,24 @@ int game_classify(game_t h, const float* chrom, const float* X, const float* y,
 
 /* Waits for the handle's stream and reports a kernel timeout, if any. */
 int game_sync(game_t h);
+
+/* Test hooks: process-wide switches that make the library's failure paths
+ * reachable without any fault on the GPU (the paper has no counterpart).
+ *   GAME_HOOK_FAIL_ALLOC, value k >= 1: the k-th device allocation made by
+ *     the library from now on fails as if the device were out of memory
+ *     (the call then returns GAME_ENOMEM after releasing what it holds);
+ *     0 switches the hook off.
+ *   GAME_HOOK_STALL_NS, value t in 1..10^9: the next launch of the
+ *     tensor-core fitness kernel makes its MMA issuer wait up to t ns on a
+ *     barrier phase that nothing completes; the wait runs out, and the kernel
+ *     abandons the launch the way every expired wait does (raises the
+ *     handle's status word, drains its own copies and MMAs, frees its tensor
+ *     memory, returns), so the call reports GAME_ETIMEOUT and the handle
+ *     stays usable; 0 cancels a pending stall.
+ * Returns GAME_EINVAL for an unknown hook or a value out of range. */
+#define GAME_HOOK_FAIL_ALLOC 1
+#define GAME_HOOK_STALL_NS 2
+int game_test_hook(int32_t hook, int64_t value);
 
 /* Releases the handle and all its device memory (NULL is accepted). */
 int game_destroy(game_t h);

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -23,6 +24,20 @@ namespace game {
 // Sets the calling thread's game_last_error() text (used by entry points
 // defined outside this file).
 void record_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+std::atomic<int64_t> g_alloc_countdown{0};   // > 0: allocations until the failing one
+std::atomic<uint64_t> g_stall_ns{0};
+}  // namespace
+
+bool hook_alloc_fails() {
+  int64_t n = g_alloc_countdown.load();
+  while (n > 0 && !g_alloc_countdown.compare_exchange_weak(n, n - 1)) {
+  }
+  return n == 1;
+}
+
+uint64_t hook_take_stall_ns() { return g_stall_ns.exchange(0); }
 }  // namespace game
 
 namespace {
@@ -57,6 +72,7 @@ template <typename T>
 cudaError_t dev_alloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (hook_alloc_fails()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
@@ -697,6 +713,20 @@ int copy_in(game_ctx* h, void* dst, const void* src, size_t bytes) {
 extern "C" {
 
 const char* game_last_error(void) { return g_last_error.c_str(); }
+
+int game_test_hook(int32_t hook, int64_t value) {
+  g_last_error.clear();
+  if (value < 0) return fail(GAME_EINVAL, "hook value must be >= 0");
+  if (hook == GAME_HOOK_FAIL_ALLOC) {
+    g_alloc_countdown.store(value);
+  } else if (hook == GAME_HOOK_STALL_NS) {
+    if (value > 1000000000) return fail(GAME_EINVAL, "stall limited to 1 s");
+    g_stall_ns.store((uint64_t)value);
+  } else {
+    return fail(GAME_EINVAL, "unknown hook");
+  }
+  return GAME_OK;
+}
 
 int game_params_default(game_params* out) {
   if (!out) return fail(GAME_EINVAL, "out is NULL");

@@ -209,6 +209,8 @@ int bfail(int code, const std::string& msg) {
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (hook_alloc_fails()) return cudaErrorMemoryAllocation;
   return cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T));
 }
 void dfree(void* p) {

@@ -1,21 +1,26 @@
 // fitness_static.cu -- FP32 fitness evaluation that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while another
-// component is capturing the stream into a CUDA graph (an allocation there
-// would fail or be captured), plug-ins that live under a host application's
-// fixed device-memory budget, and runtimes that forbid allocation after
-// start-up. game_eval_fitness_static serves them: the caller passes device
-// pointers to its own inputs and output, the kernel reads the inputs in
-// their natural layout (X row-major, pop [P][K]), and the one intermediate
-// buffer -- the per-CTA FP64 partial sums of squared residuals -- is the
-// file-scope array g_static_part below, of fixed size (4 MiB). Every GPU that
-// loads the library holds that array until the process exits.
+// Some callers cannot call cudaMalloc: plug-ins that live inside a host
+// application which owns the whole device-memory budget and hands out only
+// what it pre-allocated, runtimes that forbid allocation after start-up (an
+// allocation can fail, and cudaMalloc / cudaFree may synchronise the device,
+// which stalls every other stream of the process), and code that must not
+// change the device's memory footprint while other work runs.
+// game_eval_fitness_static serves them: the caller passes device pointers to
+// its own inputs and output, the kernel reads the inputs in their natural
+// layout (X row-major, pop [P][K]), and the one intermediate buffer -- the
+// per-CTA FP64 partial sums of squared residuals -- is the file-scope array
+// g_static_part below, of fixed size (4 MiB). Every GPU that loads the
+// library holds that array until the process exits.
 //
 // Its first call on a device looks the array's device address up
 // (cudaGetSymbolAddress, with that device current) and caches it; make that
-// first call before any stream capture. All calls share the array: calls
-// that overlap on the GPU (different streams, or different host threads on
-// one device) race on it and must be serialised by the caller. Each call
+// first call before any stream capture. The cached address belongs to the
+// device's primary context: after cudaDeviceReset the module is loaded
+// anew and the address may change, so no call may follow a reset of that
+// device in the same process. All calls share the array: calls that
+// overlap on the GPU (different streams, or different host threads on one
+// device) race on it and must be serialised by the caller. Each call
 // overwrites every entry it later reads, so nothing needs clearing between
 // calls.
 #include <stdio.h>
@@ -193,19 +198,29 @@ int eval_fitness_static(const float* X, const float* y, int64_t M, int32_t N, in
     return fail(GAME_EINVAL,
                 "P exceeds the static scratch: at most 524288 chromosomes (4 MiB of partials)");
   if (M > ((int64_t)1 << 40)) return fail(GAME_EINVAL, "M too large");
-  const void* ptrs[4] = {X, y, pop, fit_out};
-  for (const void* p : ptrs) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess ||
-        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-      cudaGetLastError();
-      return fail(GAME_EINVAL, "X, y, pop and fit_out must be device pointers");
-    }
-  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(GAME_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(GAME_EINVAL, "device ordinal beyond 63");
+  // every array must be device memory of the current device (managed memory
+  // is reachable from any device): a pointer into another GPU would make the
+  // kernel read or write that GPU's memory
+  const void* ptrs[4] = {X, y, pop, fit_out};
+  const char* names[4] = {"X", "y", "pop", "fit_out"};
+  for (int i = 0; i < 4; ++i) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return fail(GAME_EINVAL, "X, y, pop and fit_out must be device pointers");
+    }
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+      snprintf(g_static_err, sizeof(g_static_err),
+               "%s is memory of device %d, not of the current device %d", names[i], at.device,
+               dev);
+      return GAME_EINVAL;
+    }
+  }
   double* part = nullptr;
   int sms = 0;
   {

@@ -98,6 +98,8 @@ struct TcArgs {
   const float* colinv;   // FP8 only, [KB * 128]
   double* part;
   int* status;
+  uint64_t stall_ns;   // test hook: > 0 makes the MMA issuer first wait this long on a
+                       // barrier phase that nothing completes, then abandon the launch
 };
 
 struct SmemPlan {
@@ -234,6 +236,19 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       const int nlast = a.nmma_last;
       uint32_t s = 0, ph = 0, acc_it = 0;   // A stage and its phase, accumulator count
       bool ok = true;
+      if (a.stall_ns) {
+        // test hook: the drain barrier's first phase completes only at the
+        // final commit below, so this wait runs out; the launch is then
+        // abandoned as on any expired wait (status word, abort flag)
+        const uint64_t t0 = ptx::global_timer_ns();
+        while (ok && !ptx::mbar_try_wait_sleep(ptx::smem_addr(drain), 0, kSuspendNs)) {
+          if (ptx::global_timer_ns() - t0 > a.stall_ns) {
+            *abort_flag = 1;
+            atomicExch(a.status, (int)kDevTimeout);
+            ok = false;
+          }
+        }
+      }
       // one K step (32 bytes of each operand row): one MMA, three for bf16x3
       auto kstep = [&](uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
         if (F == kFormFP8) {
@@ -826,6 +841,7 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.colinv = colinv;
   a.part = part;
   a.status = status;
+  a.stall_ns = hook_take_stall_ns();
   if (pl.form == kFormFP8 && (!uscale || !colinv)) return cudaErrorInvalidValue;
   if (pl.BN == 192 && pl.form != kFormBF16) return cudaErrorInvalidValue;
   if (pl.NS < pl.KB || pl.NS > 2 * pl.KB) return cudaErrorInvalidValue;

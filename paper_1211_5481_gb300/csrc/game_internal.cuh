@@ -52,6 +52,14 @@ struct Shape {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// ---- test hooks (game_test_hook, api.cu) ----
+// True when the device allocation about to be made is the one the
+// allocation-failure hook picked (each call counts one allocation).
+bool hook_alloc_fails();
+// The stall (ns) the next tensor-core fitness launch is to make, 0 for
+// none; taking it clears it.
+uint64_t hook_take_stall_ns();
+
 // ---- kernels and launchers (defined in the .cu files) ----
 // layout.cu
 cudaError_t launch_relayout_X(const float* X, const float* y, const Shape& s, float* Xt,

@@ -35,6 +35,8 @@ GAME_ERR_MAE = 2
 GAME_SEL_TOURNAMENT = 0
 GAME_SEL_RANKING = 1
 GAME_SEL_ROULETTE = 2
+GAME_HOOK_FAIL_ALLOC = 1
+GAME_HOOK_STALL_NS = 2
 
 _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
               GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}
@@ -49,7 +51,7 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_batch_destroy", "game_surrogate_predict", "game_surrogate_grad",
             "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
             "game_surrogate_last", "game_gram", "game_predict", "game_classify",
-            "game_save", "game_load")
+            "game_save", "game_load", "game_test_hook")
 
 
 class GameError(RuntimeError):
@@ -180,6 +182,7 @@ def load(build_if_missing: bool = True):
         "game_predict": [vp, vp, vp, i64, dp],
         "game_save": [vp, ctypes.c_char_p],
         "game_load": [vp, ctypes.c_char_p],
+        "game_test_hook": [i32, i64],
         "game_classify": [vp, vp, vp, vp, i64, ctypes.c_double, ctypes.POINTER(game_confusion)],
     }
     for name, args in sig.items():
@@ -319,18 +322,42 @@ def game_get_timing(h) -> dict:
 
 
 def game_eval_fitness_static(X, y, degree: int, basis: int, pop, fit_out, stream=None):
-    """Allocation-free FP32 fitness; all arrays are CUDA tensors."""
-    M, N = X.shape
+    """Allocation-free FP32 fitness. X [M][N], y [M], pop [P][K] float32 and
+    fit_out [>= P] float64, all contiguous CUDA tensors (the library reads
+    them through raw pointers, so every shape is checked here first)."""
     for a, dt, name in ((X, "float32", "X"), (y, "float32", "y"), (pop, "float32", "pop"),
                         (fit_out, "float64", "fit_out")):
         _need(a, dt, name)
+        if not getattr(a, "is_cuda", False):
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if X.dim() != 2 or pop.dim() != 2:
+        raise ValueError("X and pop must be 2-D")
+    M, N = X.shape
+    B = 2 if basis == GAME_BASIS_TRIG else 1
+    K = B * N * degree + 1
+    P = pop.shape[0]
+    if y.numel() != M:
+        raise ValueError(f"y has {y.numel()} elements, X has {M} rows")
+    if pop.shape[1] != K:
+        raise ValueError(f"pop has {pop.shape[1]} genes per chromosome, B*N*d + 1 = {K}")
+    if fit_out.numel() < P:
+        raise ValueError(f"fit_out holds {fit_out.numel()} values, P = {P}")
     _check(load().game_eval_fitness_static(_ptr(X), _ptr(y), M, N, degree, basis, _ptr(pop),
-                                           pop.shape[0], _ptr(fit_out), _stream_ptr(stream)))
+                                           P, _ptr(fit_out), _stream_ptr(stream)))
     return fit_out
 
 
 def game_sync(h):
     _check(load().game_sync(h))
+
+
+def game_test_hook(hook: int, value: int):
+    """Arms a test hook (GAME_HOOK_FAIL_ALLOC: the value-th device
+    allocation from now fails; GAME_HOOK_STALL_NS: the next tensor-core
+    fitness launch runs into an expired wait after value ns; 0 = off)."""
+    _check(load().game_test_hook(hook, value))
 
 
 def game_destroy(h):

@@ -8,6 +8,7 @@ CHEB, TRIG = 0, 1
 U_BF16 = 2.0 ** -8   # unit roundoff of bfloat16 (8 significant bits)
 U_FP32 = 2.0 ** -24
 U_E4M3 = 2.0 ** -4   # unit roundoff of FP8 E4M3 (4 significant bits)
+U64 = 2.0 ** -53
 
 
 def design_matrix(X, d, basis, dtype=np.float64):
@@ -88,3 +89,15 @@ def bf16_bound(f_oracle, X, pop, d, basis):
     e = 2 * U_BF16 + U_BF16 ** 2 + K * U_FP32
     ms = abs_weighted_sum(X, pop, d, basis) * e * e
     return 2 * np.sqrt(np.asarray(f_oracle)) * np.sqrt(ms) + ms
+
+
+def quad_bound(G, b, yy, pop, M):
+    """|fit - fit_exact| <= c u (y.y + 2 |a|.|b| + |a|^T |G| |a|) / M with
+    c = 4 (K + 8): each of the three sums carries at most K + 8 roundings
+    of its own magnitude in FP64, plus the rounding of G and b themselves
+    (their accumulation over the patterns, bounded the same way relative to
+    the absolute sums, which |G| and |b| dominate)."""
+    A = np.abs(np.asarray(pop, dtype=np.float64))
+    K = A.shape[1]
+    mag = yy + 2 * A @ np.abs(b) + np.einsum("pk,kl,pl->p", A, np.abs(G), A)
+    return 4 * (K + 8) * U64 * mag / M + 1e-300

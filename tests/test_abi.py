@@ -213,7 +213,7 @@ def test_every_entry_point_refuses_a_null_handle():
     GAME_EINVAL with a message; destroying NULL is a no-op."""
     lib = game.load()
     skip = {"game_last_error", "game_params_default", "game_create", "game_batch_create",
-            "game_eval_fitness_static"}
+            "game_eval_fitness_static", "game_test_hook"}
     for name in game.EXPORTED:
         if name in skip:
             continue
@@ -226,3 +226,15 @@ def test_every_entry_point_refuses_a_null_handle():
         else:
             assert rc == game.GAME_EINVAL, name
             assert lib.game_last_error(), name
+
+
+def test_test_hook_refusals():
+    """The test hooks take no handle: unknown hooks and out-of-range values
+    are refused; 0 disarms each (left disarmed for the rest of the run)."""
+    lib = game.load()
+    assert lib.game_test_hook(99, 1) == game.GAME_EINVAL
+    assert lib.game_test_hook(game.GAME_HOOK_FAIL_ALLOC, -1) == game.GAME_EINVAL
+    assert lib.game_test_hook(game.GAME_HOOK_STALL_NS, 2_000_000_000) == game.GAME_EINVAL
+    assert lib.game_last_error()
+    assert lib.game_test_hook(game.GAME_HOOK_FAIL_ALLOC, 0) == game.GAME_OK
+    assert lib.game_test_hook(game.GAME_HOOK_STALL_NS, 0) == game.GAME_OK

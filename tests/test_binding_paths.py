@@ -111,3 +111,49 @@ def test_batch_methods(stand_in):
         assert b.tiles().shape == (2,)
         b.fitness_ms()
         b.sync()
+
+
+class _OnDevice:
+    """A CPU tensor that reports itself as a CUDA tensor: the allocation-free
+    wrapper checks device residence, contiguity and shapes before it takes
+    raw pointers, and the stand-in library never dereferences them."""
+
+    def __init__(self, t):
+        self.t = t
+        self.dtype, self.shape, self.is_cuda = t.dtype, t.shape, True
+
+    def dim(self):
+        return self.t.dim()
+
+    def numel(self):
+        return self.t.numel()
+
+    def is_contiguous(self):
+        return self.t.is_contiguous()
+
+    def data_ptr(self):
+        return self.t.data_ptr()
+
+
+def test_static_wrapper_checks_shapes(stand_in):
+    f32, f64 = torch.float32, torch.float64
+    M, N, d = 50, 3, 2
+    K = 2 * N * d + 1          # trigonometric basis
+    X, y = torch.zeros((M, N), dtype=f32), torch.zeros(M, dtype=f32)
+    pop, fit = torch.zeros((6, K), dtype=f32), torch.zeros(6, dtype=f64)
+    dv = _OnDevice
+    trig = game.GAME_BASIS_TRIG
+    out = game.game_eval_fitness_static(dv(X), dv(y), d, trig, dv(pop), dv(fit))
+    assert out.t is fit
+    with pytest.raises(TypeError):          # host tensors
+        game.game_eval_fitness_static(X, dv(y), d, trig, dv(pop), dv(fit))
+    with pytest.raises(TypeError):          # element type
+        game.game_eval_fitness_static(dv(X), dv(y), d, trig, dv(pop.double()), dv(fit))
+    with pytest.raises(ValueError):         # K of the Chebyshev basis, not the trigonometric one
+        game.game_eval_fitness_static(dv(X), dv(y), d, game.GAME_BASIS_CHEB, dv(pop), dv(fit))
+    with pytest.raises(ValueError):         # y shorter than X
+        game.game_eval_fitness_static(dv(X), dv(y[:-1]), d, trig, dv(pop), dv(fit))
+    with pytest.raises(ValueError):         # fit_out shorter than P
+        game.game_eval_fitness_static(dv(X), dv(y), d, trig, dv(pop), dv(fit[:5]))
+    with pytest.raises(ValueError):         # a transposed (strided) view
+        game.game_eval_fitness_static(dv(X.t()), dv(y), d, trig, dv(pop), dv(fit))

@@ -36,7 +36,17 @@ CASES = [
     (2999, 9, 8, CHEB, 130),     # K' = 72: the last MMA reads a zero chunk
     (1500, 3, 16, CHEB, 64),     # degree 16: chunks starting at degree 9
     (3000, 48, 8, CHEB, 200),    # K' = 384: 128-pattern tiles, ten slots
+    # the narrowest tiles of every form, each at its longest contraction
+    (1500, 128, 20, CHEB, 40),   # K' = 2560: BF16 at its limit, 32-pattern tiles
+    (1300, 66, 10, TRIG, 70),    # K' = 1320: BF16 32-pattern tiles, trigonometric
+    (1203, 64, 19, CHEB, 130),   # K' = 1216: bf16x3 at its limit, 32-pattern tiles
+    (1100, 128, 32, CHEB, 40),   # K' = 4096: FP8 at its limit, 32-pattern tiles
+    (2500, 50, 10, CHEB, 200),   # K' = 500: FP8 128-pattern tiles
 ]
+
+# longest contraction K' each tensor-core form accepts at N <= 128 (the
+# expansion tile of all K' columns stays in shared memory)
+KP_LIMIT = {BF16: 2560, BF16X3: 1216, FP8: 4096, FP32: 4096}
 
 
 def make_problem(M, N, d, basis, seed):
@@ -58,8 +68,8 @@ def test_fitness_matches_oracle(orc, dev, case, prec):
     pr = make_problem(M, N, d, basis, seed=M + N + d)
     pop = dg.random_population(7 + P, P, pr.K)
     ref = orc.fitness(pr.X, pr.y, pop, d, basis)
-    if prec == BF16X3 and pr.K - 1 > 1216:
-        # both split operands no longer fit in shared memory: rejected
+    if pr.K - 1 > KP_LIMIT[prec]:
+        # the expansion tile no longer fits in shared memory: rejected
         with pytest.raises(game.GameError) as ei:
             game.Game(pr.X, pr.y, d, basis, P=max(P, 4), precision=prec)
         assert ei.value.code == game.GAME_EINVAL
@@ -73,6 +83,23 @@ def test_fitness_matches_oracle(orc, dev, case, prec):
     err = np.abs(got - ref)
     assert np.all(err <= tol), (f"max err {err.max():.3e}, worst ratio "
                                 f"{(err / tol).max():.3f}, rel {np.max(err / np.abs(ref)):.3e}")
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16, BF16X3, FP8], ids=["fp32", "bf16", "bf16x3", "fp8"])
+def test_trigonometric_wide_domain(orc, dev, prec):
+    """Eq. 6 puts no limit on x: features spread over [-8, 8] exercise the
+    argument reduction of sincosf and the recurrences far from [-1, 1]."""
+    pr = dg.regression(41, 3000, 6, 3, 0.05, degree=5, basis=TRIG)
+    X = (pr.X * np.float32(8.0)).astype(np.float32)
+    assert np.abs(X).max() > 7.5
+    P = 100
+    pop = dg.random_population(43, P, pr.K)
+    ref = orc.fitness(X, pr.y, pop, 5, TRIG)
+    with game.Game(X, pr.y, 5, TRIG, P=P, precision=prec) as g:
+        got = g.eval_fitness(pop)
+    tol = fp32_tol(ref, pr.y) if prec == FP32 else BOUNDS[prec](ref, X, pop, 5, TRIG)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (f"max err {err.max():.3e}, worst ratio {(err / tol).max():.3f}")
 
 
 def test_device_and_host_pointers_agree(dev):

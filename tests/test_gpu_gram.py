@@ -5,14 +5,13 @@ FP64 rounding bound of the quadratic form."""
 import numpy as np
 import pytest
 
-from helpers import CHEB, TRIG
+from helpers import CHEB, TRIG, U64, quad_bound
 from paper_1211_5481_gb300 import datagen as dg
 from paper_1211_5481_gb300 import game
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GRAM = game.GAME_PREC_GRAM
-U64 = 2.0 ** -53
 
 CASES = [
     (2000, 8, 4, CHEB, 64),
@@ -22,18 +21,6 @@ CASES = [
     (70001, 6, 5, CHEB, 33),    # several chunks of patterns? (one; rows split 8 ways)
     (3001, 48, 6, CHEB, 300),
 ]
-
-
-def quad_bound(G, b, yy, pop, M):
-    """|fit - fit_exact| <= c u (y.y + 2 |a|.|b| + |a|^T |G| |a|) / M with
-    c = 4 (K + 8): each of the three sums carries at most K + 8 roundings
-    of its own magnitude in FP64, plus the rounding of G and b themselves
-    (their accumulation over the patterns, bounded the same way relative to
-    the absolute sums, which |G| and |b| dominate)."""
-    A = np.abs(np.asarray(pop, dtype=np.float64))
-    K = A.shape[1]
-    mag = yy + 2 * A @ np.abs(b) + np.einsum("pk,kl,pl->p", A, np.abs(G), A)
-    return 4 * (K + 8) * U64 * mag / M + 1e-300
 
 
 @pytest.mark.parametrize("case", CASES, ids=[str(c) for c in CASES])

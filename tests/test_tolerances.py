@@ -11,25 +11,9 @@ change making them vacuous fails here."""
 import numpy as np
 import pytest
 
+from emulation import bf16, e4m3
 from helpers import CHEB, TRIG, bf16_bound, bf16x3_bound, design_matrix, fp8_bound
 from paper_1211_5481_gb300 import datagen as dg
-
-
-def bf16(x):
-    f = np.asarray(x, dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32)
-
-
-def e4m3(x):
-    """Round to the nearest E4M3 value (3 fraction bits, subnormal quantum
-    2^-9), ties to even, saturating at 448."""
-    x = np.asarray(x, dtype=np.float64)
-    a = np.abs(x)
-    e = np.maximum(np.floor(np.log2(np.maximum(a, 2.0 ** -9))), -6)
-    q = 2.0 ** (e - 3)
-    return (np.sign(x) * np.minimum(np.round(a / q) * q, 448.0)).astype(np.float32)
 
 
 def fitness_from_products(y, a0, D):

@@ -1,10 +1,12 @@
 """game_eval_fitness_static: the fitness call for callers that cannot
-allocate device memory (code running under someone else's stream capture,
-plug-ins with a fixed device-memory budget, runtimes that forbid allocation
-after start-up). It keeps its only scratch, the FP64 partial sums, in a
-fixed array inside the library, so its results must match the ordinary
-handle-based FP32 evaluation on the same inputs, call after call, with
-nothing left over from the previous call.
+allocate device memory -- plug-ins inside a host application that owns the
+device-memory budget, and runtimes that forbid allocation after start-up
+(cudaMalloc can fail and may synchronise the device). It keeps its only
+scratch, the FP64 partial sums, in a fixed array inside the library, so two
+calls in a row must each give what the ordinary handle-based FP32
+evaluation (game_eval_fitness) gives on the same inputs, and both must match
+the FP64 oracle within the FP32 tolerance, with nothing left over from the
+previous call.
 
 This file is named to be collected last: if it fails, a run that stops at
 the first failure has already run every other test."""
@@ -29,7 +31,7 @@ def _static_call(lib, Xd, yd, d, basis, popd, fitd, stream):
 
 
 @pytest.mark.parametrize("M,N,d,basis,P", [(5003, 6, 5, CHEB, 200), (2000, 3, 4, TRIG, 70)])
-def test_static_matches_handle_path_two_calls(M, N, d, basis, P):
+def test_static_matches_handle_path_two_calls(orc, M, N, d, basis, P):
     assert torch.cuda.is_available()
     lib = game.load()
     dev = torch.device("cuda:0")
@@ -39,9 +41,10 @@ def test_static_matches_handle_path_two_calls(M, N, d, basis, P):
     yd = torch.from_numpy(pr.y).to(dev)
     pops = [dg.random_population(1 + s, P, pr.K) for s in range(2)]
     with game.Game(pr.X, pr.y, d, basis, P=max(P, 4), precision=game.GAME_PREC_FP32) as g:
-        refs = [g.eval_fitness(p) for p in pops]
+        handle = [g.eval_fitness(p) for p in pops]
+    oracle = [orc.fitness(pr.X, pr.y, p, d, basis) for p in pops]
     # two calls in a row on different populations through the C ABI
-    for pop, ref in zip(pops, refs):
+    for pop, ref, exact in zip(pops, handle, oracle):
         popd = torch.from_numpy(pop).to(dev)
         fitd = torch.full((P,), float("nan"), dtype=torch.float64, device=dev)
         rc = _static_call(lib, Xd, yd, d, basis, popd, fitd, stream)
@@ -50,6 +53,8 @@ def test_static_matches_handle_path_two_calls(M, N, d, basis, P):
         got = fitd.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.all(np.abs(got - ref) <= fp32_tol(ref, pr.y)), np.max(np.abs(got - ref) / ref)
+        assert np.all(np.abs(got - exact) <= fp32_tol(exact, pr.y)), \
+            np.max(np.abs(got - exact) / exact)
 
 
 def test_static_rejects_oversized_and_host_inputs():

@@ -65,6 +65,12 @@ def parse():
                     help="surrogate workload: also run G generations of the FP64 oracle GA "
                          "(Gram form) and of the screened GPU GA and compare the best fitness")
     ap.add_argument("--no-fp32-leg", action="store_true")
+    ap.add_argument("--no-surrogate-leg", action="store_true",
+                    help="classification workload at one GPU: skip the surrogate workload's "
+                         "legs (4M patterns, screened BF16 vs plain FP32) added to the line")
+    ap.add_argument("--surrogate-oracle-run", type=int, default=300, metavar="G",
+                    help="surrogate legs: generations of the final-best comparison with the "
+                         "FP64 oracle GA (0 = off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--precision-report", type=int, default=4, metavar="G",
@@ -76,10 +82,30 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM bytes per launch of the dominant kernel, read + write, from the ncu
-# capture summarised in profiles/fitness_tc_M1000000_N32_cheb8_P1024_ncu.md
-# (valid for that kernel version and workload only; None elsewhere)
-NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): 132.71e6 + 3.09e6}
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture), per workload and form, with the
+# digest of the kernel sources the capture ran: reported only while the
+# sources are unchanged (null once the kernel has changed since).
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): (132.71e6 + 3.09e6, "unrecorded")}
+KERNEL_SOURCES = ("fitness_tc.cu", "tc_common.cuh", "tc_ptx.cuh", "basis.cuh",
+                  "game_internal.cuh")
+
+
+def kernel_digest():
+    """sha256 (first 16 hex digits) of the fused fitness kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1211_5481_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, form):
+    entry = NCU_TRAFFIC.get((workload, form))
+    if entry is None or entry[1] != kernel_digest():
+        return None
+    return entry[0]
 
 
 def max_over_ranks(t, world, dev=None):
@@ -381,23 +407,34 @@ def spearman(a, b):
     return float(np.corrcoef(ra, rb)[0, 1])
 
 
-def run_surrogate(args, torch, game, dev, world, rank):
-    """The surrogate-screened form (BF16 contraction, elite re-scoring, 8x
+def oracle_ga_best(pr, G):
+    """Best fitness after G generations of the FP64 oracle GA on problem pr
+    (Gram-form fitness, no surrogate, seed 4), and its host time."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    _, _, best = oracle.train(pr.X, pr.y, pr.degree, pr.basis, pr.P, G, 4, use_gram=True)
+    return {"generations": G, "best": float(best[-1]), "seconds": time.perf_counter() - t0,
+            "cores": oracle.set_threads(0)}
+
+
+def surrogate_leg(torch, game, dev, pr, Xd, yd, oversample, steps_per_gen, timed_gens,
+                  warmup, oracle_final=None, precision_gens=0, fp32_gens=3, clocks_enabled=True,
+                  cpu_reports=True):
+    """The surrogate-screened form (BF16 contraction, elite re-scoring,
     oversampled offspring screened by the MLP) against the plain FP32 form
-    on the 4M-pattern regression set (N = 48, Chebyshev degree 6, K = 289,
-    P = 2048): generations per second of each, the ratio, the surrogate's
-    rank agreement with the exact fitness of the children it kept, and the
-    accuracy of the BF16 form against the FP64 oracle on 10,000 patterns."""
-    from paper_1211_5481_gb300 import datagen as dg
-    pr = dg.surrogate_regression()
-    M, K, P = pr.M, pr.K, pr.P
+    on the surrogate workload: generations per second of each and their
+    ratio, the surrogate's rank correlation with the exact fitness of the
+    children it kept and its trust verdicts, per-generation accuracy of the
+    contraction forms against the FP64 oracle on 10,000 patterns, and, given
+    oracle_final, the best fitness after its G generations of the screened
+    GA against the FP64 oracle GA's (oracle_final, from oracle_ga_best)."""
+    M, P = pr.M, pr.P
     stream = torch.cuda.current_stream(dev)
-    Xd = torch.from_numpy(pr.X).to(dev)
-    yd = torch.from_numpy(pr.y).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def timed(h, steps, warmup):
-        for _ in range(warmup):
+    def timed(h, steps, warm):
+        for _ in range(warm):
             game.game_generation(h.h, 4)
         torch.cuda.synchronize(dev)
         h.set_timing(True)
@@ -415,15 +452,15 @@ def run_surrogate(args, torch, game, dev, world, rank):
         h.set_timing(False)
         return sum(x.elapsed_time(y) for x, y in ev) / len(ev), tm
 
-    gs = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                   precision=game.GAME_PREC_BF16, surrogate=1, oversample=args.oversample,
-                   surrogate_steps=args.surrogate_steps)
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
-    t_sur, tm = timed(gs, args.steps, max(args.warmup, 3))
+    kw = dict(stream=stream, P=P, seed=4, precision=game.GAME_PREC_BF16, surrogate=1,
+              oversample=oversample, surrogate_steps=steps_per_gen)
+    gs = game.Game(Xd, yd, pr.degree, pr.basis, **kw)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=clocks_enabled)
+    t_sur, tm = timed(gs, timed_gens, warmup)
     clk = clocks.stop()
     g32 = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
                     precision=game.GAME_PREC_FP32)
-    t_32, _ = timed(g32, max(3, args.steps // 10), 1)
+    t_32, _ = timed(g32, fp32_gens, 1)
     g32.close()
     # surrogate rank agreement on the next generations (untimed)
     rho, trust = [], []
@@ -434,53 +471,74 @@ def run_surrogate(args, torch, game, dev, world, rank):
         _, fit, _ = gs.population()
         rho.append(spearman(pred[keep.astype(bool)], np.log(fit[E:])))
         trust.append({"trusted": trusted, "pearson_kept": r})
-    acc = None
-    if rank == 0 and not args.no_cpu_baseline:
-        acc = precision_report(game, gs, pr, 2)
+    acc = precision_report(game, gs, pr, precision_gens) if cpu_reports and precision_gens else None
+    gs.close()
     final = None
-    if rank == 0 and args.oracle_run > 0:
-        import oracle
-        oracle.build()
-        G = args.oracle_run
+    if oracle_final is not None:
+        G = oracle_final["generations"]
+        gg = game.Game(Xd, yd, pr.degree, pr.basis, **kw)
         t0 = time.perf_counter()
-        _, _, best_o = oracle.train(pr.X, pr.y, pr.degree, pr.basis, P, G, 4, use_gram=True)
-        t_o = time.perf_counter() - t0
-        gg = game.Game(Xd, yd, pr.degree, pr.basis, stream=stream, P=P, seed=4,
-                       precision=game.GAME_PREC_BF16, surrogate=1, oversample=args.oversample,
-                       surrogate_steps=args.surrogate_steps)
         gg.train(G)
+        t_g = time.perf_counter() - t0
         _, fit_g, _ = gg.population()
         gg.close()
-        best_g = float(fit_g.min())
-        final = {"generations": G, "oracle_best": float(best_o[-1]), "screened_bf16_best": best_g,
-                 "rel_diff": (best_g - float(best_o[-1])) / float(best_o[-1]),
+        best_g, best_o = float(fit_g.min()), oracle_final["best"]
+        final = {"generations": G, "oracle_best": best_o, "screened_bf16_best": best_g,
+                 "rel_diff": (best_g - best_o) / best_o,
                  "oracle": "FP64 GA, Gram-form fitness, no surrogate, same seed",
-                 "oracle_s": t_o}
+                 "oracle_s": oracle_final["seconds"], "gpu_s": t_g}
     gen_s, gen32_s = 1e3 / t_sur, 1e3 / t_32
+    return {
+        "workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": pr.K, "P": P,
+        "form": f"BF16 contraction + elite re-score + surrogate screening, "
+                f"{oversample}x oversampled offspring, {steps_per_gen} Adam round(s) "
+                f"per generation",
+        "oversample": oversample, "surrogate_steps": steps_per_gen,
+        "ms_per_generation": t_sur, "generations_per_s": gen_s, "evals_per_s": M * P / (t_sur * 1e-3),
+        "fp32_form": {"ms_per_generation": t_32, "generations_per_s": gen32_s},
+        "gens_ratio_vs_fp32": gen_s / gen32_s,
+        "stage_ms_per_generation": {k.replace("_ms", ""): tm[k] / max(timed_gens, 1)
+                                    for k in ("fitness_ms", "pack_ms", "reduce_ms",
+                                              "operators_ms", "rescore_ms", "surrogate_ms")},
+        "surrogate_rank_spearman_kept": rho, "surrogate_trust": trust,
+        "accuracy": acc, "final_best": final, "clocks": clk,
+        "timing": "CUDA events around each generation, L2 flushed between generations",
+    }
+
+
+def run_surrogate(args, torch, game, dev, world, rank):
+    """The surrogate workload (4M patterns, N = 48, Chebyshev degree 6,
+    K = 289, P = 2048) as its own JSON line: value = evaluations per second
+    of the screened generation."""
+    from paper_1211_5481_gb300 import datagen as dg
+    pr = dg.surrogate_regression()
+    Xd = torch.from_numpy(pr.X).to(dev)
+    yd = torch.from_numpy(pr.y).to(dev)
+    cpu = rank == 0 and not args.no_cpu_baseline
+    ofinal = oracle_ga_best(pr, args.oracle_run) if cpu and args.oracle_run > 0 else None
+    leg = surrogate_leg(torch, game, dev, pr, Xd, yd, args.oversample, args.surrogate_steps,
+                        args.steps, max(args.warmup, 3), oracle_final=ofinal,
+                        precision_gens=2, fp32_gens=max(3, args.steps // 10),
+                        clocks_enabled=not args.no_clocks, cpu_reports=cpu)
+    t_sur = leg["ms_per_generation"]
     line = {
-        "metric": METRIC, "value": M * P * world / (t_sur * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": pr.M * pr.P * world / (t_sur * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": t_sur, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": pr.name, "M": M, "N": pr.N, "degree": pr.degree, "K": K, "P": P,
-                   "form": f"BF16 contraction + elite re-score + surrogate screening, "
-                           f"{args.oversample}x oversampled offspring",
-                   "oversample": args.oversample,
+        "config": {"workload": pr.name, "M": pr.M, "N": pr.N, "degree": pr.degree, "K": pr.K,
+                   "P": pr.P, "form": leg["form"], "oversample": args.oversample,
                    "surrogate_steps": args.surrogate_steps,
                    "step": "one screened generation: offspring, MLP screening, exact "
                            "fitness of the kept population, MLP training",
                    "l2": "flushed between steps (256 MB write)"},
-        "generations_per_s": gen_s,
-        "fp32_form": {"ms_per_step": t_32, "generations_per_s": gen32_s},
-        "gens_ratio_vs_fp32": gen_s / gen32_s,
-        "stage_ms_per_step": {k.replace("_ms", ""): tm[k] / max(args.steps, 1)
-                              for k in ("fitness_ms", "pack_ms", "reduce_ms", "operators_ms",
-                                        "rescore_ms", "surrogate_ms")},
-        "surrogate_rank_spearman_kept": rho,
-        "surrogate_trust": trust,
-        "accuracy": acc, "final_best": final, "clocks": clk,
+        "generations_per_s": leg["generations_per_s"],
+        "fp32_form": leg["fp32_form"], "gens_ratio_vs_fp32": leg["gens_ratio_vs_fp32"],
+        "stage_ms_per_step": leg["stage_ms_per_generation"],
+        "surrogate_rank_spearman_kept": leg["surrogate_rank_spearman_kept"],
+        "surrogate_trust": leg["surrogate_trust"],
+        "accuracy": leg["accuracy"], "final_best": leg["final_best"], "clocks": leg["clocks"],
     }
-    gs.close()
     if rank == 0:
         print(json.dumps(line))
 
@@ -662,7 +720,8 @@ def main():
         mma_per_product = 3.0 if prec == game.GAME_PREC_BF16X3 else 1.0
         peak = float(peaks["bf16_tflops"]) * ratio
         roof = {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved_tflops / peak, "traffic": NCU_TRAFFIC.get((pr.name, args.form)),
+                "frac": achieved_tflops / peak, "traffic": ncu_traffic(pr.name, args.form),
+                "kernel_digest": kernel_digest(),
                 "algorithmic_bytes": 4.0 * M * pr.N + 4.0 * M + 2.0 * P * (K - 1),
                 "peak_source": (f"{peak_src} bf16_tflops (burst)"
                                 + (" x 2 (FP8 / BF16 nominal ratio)" if ratio != 1.0 else "")),
@@ -772,6 +831,28 @@ def main():
                "generating_polynomial": {k: gen_res[k] for k in
                                          ("accuracy", "completeness", "contamination")},
                "definition": "positive: label > 0, predicted positive: Out > 0 (FP64)"}
+    sur = None
+    if world == 1 and not args.no_surrogate_leg:
+        # the surrogate workload (4M patterns, N = 48, degree 6, P = 2048)
+        # beside the headline: the screened BF16 form at the workload's
+        # literal 8x oversampling with one Adam round per generation, and at
+        # 2x with eight (the setting whose surrogate the trust check
+        # accepts), each against the plain FP32 form; the FP64 oracle GA's
+        # best after G generations is shared by both comparisons
+        from paper_1211_5481_gb300 import datagen as dg
+        pr4 = dg.surrogate_regression()
+        X4 = torch.from_numpy(pr4.X).to(dev)
+        y4 = torch.from_numpy(pr4.y).to(dev)
+        cpu4 = rank == 0 and not args.no_cpu_baseline
+        of = (oracle_ga_best(pr4, args.surrogate_oracle_run)
+              if cpu4 and args.surrogate_oracle_run > 0 else None)
+        sur = {}
+        for o, st in ((8, 1), (2, 8)):
+            sur[f"oversample_{o}x_steps_{st}"] = surrogate_leg(
+                torch, game, dev, pr4, X4, y4, o, st, 10, 3, oracle_final=of,
+                precision_gens=3, fp32_gens=3, clocks_enabled=not args.no_clocks,
+                cpu_reports=cpu4)
+        del X4, y4
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
@@ -796,6 +877,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "surrogate_workload": sur,
         "gpu_launches": int(n_launch),
         "clocks": clk,
     }

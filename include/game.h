@@ -225,6 +225,38 @@ int game_get_population(game_t h, float* pop_out, double* fit_out,
 int game_set_state(game_t h, const float* pop, const double* fit,
                    int64_t generation);
 
+/* ---- Pattern sharding ----
+ * The fitness of Eq. 3 is a sum over patterns, so the training set can be
+ * split into slices held by separate handles (on separate GPUs; the paper
+ * names several GPUs as future work, Section 6): each slice gives the
+ * unnormalised error sum of every chromosome, the sums of all slices added
+ * in a fixed order and divided by the total M are the fitness, and every
+ * handle then breeds the same next population from the same (seed,
+ * generation) counters. These three calls are the per-slice steps. */
+
+/* Error sums of a population over the handle's own patterns:
+ *   sse_out[p] = sum_m (y_m - Out_p(m))^2 for GAME_ERR_MSE and GAME_ERR_RMSE
+ *   handles, sum_m |y_m - Out_p(m)| for GAME_ERR_MAE; FP64, unnormalised.
+ * Computed by the handle's precision, which must be a direct form (not
+ * GAME_PREC_GRAM: GAME_EINVAL), without elite re-scoring.
+ *   pop [P][K] FP32 genes, or NULL for the handle's current population (P is
+ *   then ignored); pop and sse_out host or device (both the same kind when
+ *   pop is given). Host outputs synchronise; device ones only enqueue. */
+int game_eval_sse(game_t h, const float* pop, int32_t P, double* sse_out);
+
+/* The operators of one generation alone (those of game_generation: elitism,
+ * selection, crossover, mutation, clamping; generation g -> g + 1), without
+ * evaluating the new population. Until game_set_fitness (or
+ * game_set_state) gives it a fitness vector, game_breed returns
+ * GAME_ESTATE, and game_generation / game_train evaluate it on the
+ * handle's own patterns first. GAME_ESTATE also for surrogate handles.
+ * Enqueues only. */
+int game_breed(game_t h, uint64_t seed);
+
+/* Sets the fitness vector of the current population: fit [P] FP64, host or
+ * device (the handle's P). Host input synchronises. */
+int game_set_fitness(game_t h, const double* fit);
+
 /* Checkpoint file of the GA state: population, fitness and generation and,
  * with the surrogate, its parameters, Adam moments and step, the trust
  * check's verdict and the replay ring, so that game_load followed by the same calls

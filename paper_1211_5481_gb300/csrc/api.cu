@@ -370,11 +370,19 @@ int replicate_tied(game_ctx* h, const float* dpop, int P) {
   return GAME_OK;
 }
 
-// Enqueues the fitness of a device population dpop [P][Kg] into dfit [P].
-int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
+// Enqueues the fitness of a device population dpop [P][Kg] into dfit [P];
+// with sums, the unnormalised error sums instead (sum over the handle's
+// patterns of the squared residuals, of the absolute ones for the MAE).
+int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit,
+                bool sums = false) {
   const int err = h->prm.error;
   if (prec == GAME_PREC_GRAM && err == GAME_ERR_MAE)
     return fail(GAME_EINVAL, "the MAE has no Gram form");
+  if (prec == GAME_PREC_GRAM && sums)
+    return fail(GAME_EINVAL, "error sums need a direct form (not GAME_PREC_GRAM)");
+  // the reduce divides by rM (and takes the root for the RMSE)
+  const int64_t rM = sums ? 1 : h->s.M;
+  const int rerr = sums ? (err == GAME_ERR_MAE ? GAME_ERR_MAE : GAME_ERR_MSE) : err;
   int rc = ensure_scratch(h, P, prec);
   if (rc) return rc;
   const int Ppad = ceil_div(P, 128) * 128;
@@ -401,7 +409,7 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
                            h->st));
     stage_end(h, t0, kFitness);
     t0 = stage_begin(h);
-    CK(launch_reduce(h->part, pl.grid_y, P, Ppad, h->s.M, err, dfit, h->st));
+    CK(launch_reduce(h->part, pl.grid_y, P, Ppad, rM, rerr, dfit, h->st));
     stage_end(h, t0, kReduce);
   } else {
     const TcPlan pl = plan_tc(h->s, P, h->num_sms, tc_form(prec));
@@ -414,7 +422,7 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit) {
                          h->part, h->status, err, h->st));
     stage_end(h, t0, kFitness);
     t0 = stage_begin(h);
-    CK(launch_reduce(h->part, pl.rows, P, Ppad, h->s.M, err, dfit, h->st));
+    CK(launch_reduce(h->part, pl.rows, P, Ppad, rM, rerr, dfit, h->st));
     stage_end(h, t0, kReduce);
   }
   return GAME_OK;
@@ -557,6 +565,25 @@ int check_status(game_ctx* h) {
     CK(cudaStreamSynchronize(h->st));
     return fail(GAME_ETIMEOUT, "a kernel wait timed out; results of the affected calls are void");
   }
+  return GAME_OK;
+}
+
+// Device copies of a host population and its fitness, for P chromosomes.
+int ensure_upload(game_ctx* h, int P) {
+  if (P <= h->ucap) return GAME_OK;
+  dev_free(h->upop);
+  dev_free(h->ufit);
+  h->upop = nullptr;
+  h->ufit = nullptr;
+  h->ucap = 0;
+  if (dev_alloc(&h->upop, (size_t)P * h->Kg) != cudaSuccess ||
+      dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(h->upop);
+    h->upop = nullptr;
+    return fail(GAME_ENOMEM, "device copy of the population");
+  }
+  h->ucap = P;
   return GAME_OK;
 }
 
@@ -879,22 +906,11 @@ int game_eval_fitness_prec(game_t h, const float* pop, int32_t P, int32_t precis
   const bool dev_in = is_device_ptr(pop), dev_out = is_device_ptr(fit_out);
   if (dev_in != dev_out) return fail(GAME_EINVAL, "pop and fit_out must be in the same memory");
   if (dev_in) return eval_device(h, pop, P, precision, fit_out);
-  if (P > h->ucap) {
-    dev_free(h->upop);
-    dev_free(h->ufit);
-    h->upop = nullptr;
-    h->ufit = nullptr;
-    h->ucap = 0;
-    if (dev_alloc(&h->upop, (size_t)P * h->Kg) != cudaSuccess ||
-        dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(GAME_ENOMEM, "device copy of the population");
-    }
-    h->ucap = P;
-  }
+  int rc = ensure_upload(h, P);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->Kg * sizeof(float), cudaMemcpyHostToDevice,
                      h->st));
-  int rc = eval_device(h, h->upop, P, precision, h->ufit);
+  rc = eval_device(h, h->upop, P, precision, h->ufit);
   if (rc) return rc;
   CK(cudaMemcpyAsync(fit_out, h->ufit, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   return check_status(h);
@@ -917,19 +933,8 @@ int game_rescore_top(game_t h, const float* pop, int32_t P, double* fit, int32_t
   if (dev_in) {
     rc = rescore_device(h, pop, P, n, fit);
   } else {
-    if (P > h->ucap) {
-      dev_free(h->upop);
-      dev_free(h->ufit);
-      h->upop = nullptr;
-      h->ufit = nullptr;
-      h->ucap = 0;
-      if (dev_alloc(&h->upop, (size_t)P * h->Kg) != cudaSuccess ||
-          dev_alloc(&h->ufit, (size_t)P) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(GAME_ENOMEM, "device copy of the population");
-      }
-      h->ucap = P;
-    }
+    rc = ensure_upload(h, P);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->Kg * sizeof(float),
                        cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->ufit, fit, (size_t)P * sizeof(double), cudaMemcpyHostToDevice, h->st));
@@ -1074,6 +1079,60 @@ int game_set_state(game_t h, const float* pop, const double* fit, int64_t genera
   h->fit_valid = true;
   h->gen = generation;
   return check_status(h);
+}
+
+int game_eval_sse(game_t h, const float* pop, int32_t P, double* sse_out) {
+  g_last_error.clear();
+  if (!h || !sse_out) return fail(GAME_EINVAL, "NULL argument");
+  if (!pop) P = h->prm.P;
+  if (P < 1 || P > (1 << 24)) return fail(GAME_EINVAL, "P must be in 1..2^24");
+  const bool dev_out = is_device_ptr(sse_out);
+  if (pop && is_device_ptr(pop) != dev_out)
+    return fail(GAME_EINVAL, "pop and sse_out must be in the same memory");
+  const float* dpop = pop ? pop : h->pop[h->cur];
+  int rc;
+  if (pop && !dev_out) {
+    rc = ensure_upload(h, P);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->upop, pop, (size_t)P * h->Kg * sizeof(float), cudaMemcpyHostToDevice,
+                       h->st));
+    dpop = h->upop;
+  } else if (!dev_out) {
+    rc = ensure_upload(h, P);
+    if (rc) return rc;
+  }
+  double* dsse = dev_out ? sse_out : h->ufit;
+  rc = eval_device(h, dpop, P, h->prm.precision, dsse, true);
+  if (rc) return rc;
+  if (!dev_out)
+    CK(cudaMemcpyAsync(sse_out, dsse, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return dev_out ? GAME_OK : check_status(h);
+}
+
+int game_breed(game_t h, uint64_t seed) {
+  g_last_error.clear();
+  if (!h) return fail(GAME_EINVAL, "NULL handle");
+  if (h->prm.surrogate)
+    return fail(GAME_ESTATE, "surrogate handles breed inside game_generation only");
+  if (!h->fit_valid) return fail(GAME_ESTATE, "the current population has no fitness");
+  if (h->gen >= 0xFFFFFFFFll) return fail(GAME_ESTATE, "generation counter exhausted");
+  cudaEvent_t t0 = stage_begin(h);
+  CK(launch_generation(ga_dev(h), h->pop[h->cur], h->fit, seed, (uint32_t)h->gen, h->plan,
+                       h->pop[h->cur ^ 1], h->st));
+  stage_end(h, t0, kOperators);
+  h->cur ^= 1;
+  h->gen += 1;
+  h->fit_valid = false;
+  return GAME_OK;
+}
+
+int game_set_fitness(game_t h, const double* fit) {
+  g_last_error.clear();
+  if (!h || !fit) return fail(GAME_EINVAL, "NULL argument");
+  int rc = copy_in(h, h->fit, fit, (size_t)h->prm.P * sizeof(double));
+  if (rc) return rc;
+  h->fit_valid = true;
+  return is_device_ptr(fit) ? GAME_OK : check_status(h);
 }
 
 int game_set_timing(game_t h, int32_t enable) {

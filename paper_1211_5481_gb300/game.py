@@ -51,7 +51,8 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_batch_destroy", "game_surrogate_predict", "game_surrogate_grad",
             "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
             "game_surrogate_last", "game_gram", "game_predict", "game_classify",
-            "game_save", "game_load", "game_test_hook")
+            "game_save", "game_load", "game_test_hook", "game_eval_sse", "game_breed",
+            "game_set_fitness")
 
 
 class GameError(RuntimeError):
@@ -183,6 +184,9 @@ def load(build_if_missing: bool = True):
         "game_save": [vp, ctypes.c_char_p],
         "game_load": [vp, ctypes.c_char_p],
         "game_test_hook": [i32, i64],
+        "game_eval_sse": [vp, vp, i32, dp],
+        "game_breed": [vp, u64],
+        "game_set_fitness": [vp, dp],
         "game_classify": [vp, vp, vp, vp, i64, ctypes.c_double, ctypes.POINTER(game_confusion)],
     }
     for name, args in sig.items():
@@ -497,6 +501,36 @@ class Game:
 
     def train(self, generations):
         return game_train(self.h, generations)
+
+    # ---- pattern sharding: per-slice steps ----
+    def eval_sse(self, pop=None, out=None):
+        """Unnormalised error sums over this handle's patterns (FP64 [P]) of
+        pop (None = the current population). out: a float64 numpy array or
+        CUDA tensor to fill (default: a new numpy array)."""
+        P = self.P if pop is None else pop.shape[0]
+        if pop is not None and isinstance(pop, np.ndarray):
+            pop = np.ascontiguousarray(pop, dtype=np.float32)
+        _need(pop, "float32", "pop")
+        if out is None:
+            out = np.zeros(P, dtype=np.float64)
+        _need(out, "float64", "out")
+        if out.shape[0] < P:
+            raise ValueError("out holds fewer than P values")
+        _check(load().game_eval_sse(self.h, _ptr(pop), P, _ptr(out)))
+        return out
+
+    def breed(self, seed):
+        """The operators of one generation, without evaluating the result."""
+        _check(load().game_breed(self.h, seed))
+
+    def set_fitness(self, fit):
+        """Fitness [P] FP64 of the current population (numpy or CUDA tensor)."""
+        if isinstance(fit, np.ndarray):
+            fit = np.ascontiguousarray(fit, dtype=np.float64)
+        _need(fit, "float64", "fit")
+        if fit.shape[0] != self.P:
+            raise ValueError(f"fit has {fit.shape[0]} values, P = {self.P}")
+        _check(load().game_set_fitness(self.h, _ptr(fit)))
 
     def population(self):
         pop = np.zeros((self.P, self.K), dtype=np.float32)

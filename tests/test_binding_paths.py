@@ -82,6 +82,13 @@ def test_game_methods_with_numpy(stand_in, tmp_path):
         g.set_timing(True)
         assert "fitness_ms" in g.timing()
         g.sync()
+        assert g.eval_sse().shape == (8,) and g.eval_sse(pop).dtype == np.float64
+        g.breed(3)
+        g.set_fitness(np.zeros(8, dtype=np.float32))
+        with pytest.raises(ValueError):
+            g.set_fitness(np.zeros(7))
+        with pytest.raises(TypeError):
+            g.eval_sse(pop, out=np.zeros(8, dtype=np.float32))
 
 
 def test_game_methods_with_tensors(stand_in):

@@ -277,9 +277,17 @@ int ensure_colscales(game_ctx* h) {
   return GAME_OK;
 }
 
+// Chromosome rows of the evaluation buffers (a0, partial sums): the
+// tensor-core plan's chromosome tiles (paired-SM plans take them in pairs),
+// else whole tiles of 128.
+int padded_P(game_ctx* h, int P, int prec) {
+  if (prec == GAME_PREC_FP32 || prec == GAME_PREC_GRAM) return ceil_div(P, 128) * 128;
+  return plan_tc(h->s, P, h->num_sms, tc_form(prec)).C * 128;
+}
+
 int ensure_scratch(game_ctx* h, int P, int prec) {
   if (prec == GAME_PREC_GRAM) return ensure_gram(h);
-  const int Ppad = ceil_div(P, 128) * 128;
+  const int Ppad = padded_P(h, P, prec);
   if (Ppad > h->cap_P) {
     dev_free(h->a0);
     dev_free(h->uscale);
@@ -385,7 +393,7 @@ int eval_device(game_ctx* h, const float* dpop, int P, int prec, double* dfit,
   const int rerr = sums ? (err == GAME_ERR_MAE ? GAME_ERR_MAE : GAME_ERR_MSE) : err;
   int rc = ensure_scratch(h, P, prec);
   if (rc) return rc;
-  const int Ppad = ceil_div(P, 128) * 128;
+  const int Ppad = padded_P(h, P, prec);
   cudaEvent_t t0;
   if (prec == GAME_PREC_GRAM) {
     t0 = stage_begin(h);

@@ -753,6 +753,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 }  // namespace
 
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
+  if (form == kFormBF16 && P > 128) {
+    const TcPlan pp = plan_tc_pair(s, P, num_sms);
+    if (pp.ok) return pp;
+  }
   TcPlan pl{};
   pl.form = form;
   pl.KB = ceil_div(s.Kp, form_cols(form));
@@ -815,6 +819,7 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               double* part, int* status, int err, cudaStream_t st) {
   (void)P;
   if (!pl.ok) return cudaErrorInvalidValue;
+  if (pl.pair) return launch_fitness_tc_pair(pl, s, Xt, y, popA, a0, Ppad, part, status, err, st);
   TcArgs a;
   a.M = s.M;
   a.N = s.N;

@@ -90,9 +90,17 @@ __host__ __device__ constexpr int form_cols(int f) { return f == kFormFP8 ? 128 
 // the features are staged in shared memory, 0 when read from L2
 struct TcPlan {
   int form, BN, KB, NS, xstage, C, stages, grid, smem_bytes, tmem_cols, rows;
+  int pair;   // 1: the paired-SM kernel (fitness_tc2.cu), C even, grid of 2-CTA clusters
   bool ok;
 };
+// The launch plan of a tensor-core fitness evaluation. The BF16 form with
+// more than one chromosome tile takes the paired-SM kernel where its shared
+// memory fits; every other case the one-SM kernel. Ppad = C * 128.
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form);
+TcPlan plan_tc_pair(const Shape& s, int P, int num_sms);
+cudaError_t launch_fitness_tc_pair(const TcPlan& pl, const Shape& s, const float* Xt,
+                                   const float* y, const uint8_t* popA, const float* a0, int Ppad,
+                                   double* part, int* status, int err, cudaStream_t st);
 // err: GAME_ERR_MAE sums absolute residuals, any other value squared ones
 cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
                               const float* y, const uint8_t* popA, const float* a0,

@@ -9,8 +9,9 @@ of the form's column width; an expansion ring of KB to 2 KB slots; features
 read from L2 only for the BF16 Chebyshev runs of 8 degrees at 128 or 256
 patterns; a power-of-two TMEM allocation of at most 512 columns that holds
 two accumulators; a grid of at most one CTA per SM and per pattern tile; one
-partial row per CTA and column half; refusal monotone in the contraction
-length and independent of P. CUDA-core plan: a contraction padded to whole
+partial row per CTA and column half (per 2-CTA cluster and column half for
+the paired-SM plans of the BF16 form, whose chromosome tiles come in pairs);
+refusal monotone in the contraction length and independent of P. CUDA-core plan: a contraction padded to whole
 chunks, at least one and at most ceil(M / 128) pattern blocks."""
 import os
 import shutil
@@ -55,13 +56,17 @@ int main() {
               ++plans;
               if (pi == 0) ok0 = pl.ok;
               CHECK(pl.ok == ok0, "form %d N %d d %d: refusal depends on P", form, N, d);
-              CHECK(pl.C == (P + 127) / 128, "C");
               if (!pl.ok) continue;
+              CHECK(pl.pair == 0 || pl.pair == 1, "pair");
+              CHECK(!pl.pair || (form == kFormBF16 && P > 128), "pair plan for form %d P %d", form, P);
+              if (pl.pair) CHECK(pl.C == 2 * ((P + 255) / 256), "pair C");
+              else CHECK(pl.C == (P + 127) / 128, "C");
               CHECK(!refused, "form %d basis %d N %d d %d: accepted after a shorter K' was refused",
                     form, basis, N, d);
               CHECK(pl.smem_bytes <= 232448 && pl.smem_bytes >= 120 * 1024, "smem %d", pl.smem_bytes);
               CHECK(pl.BN == 256 || pl.BN == 192 || pl.BN == 128 || pl.BN == 64 || pl.BN == 32,
                     "BN %d", pl.BN);
+              CHECK(!pl.pair || pl.BN == 256, "pair tile %d", pl.BN);
               CHECK(768 % pl.BN == 0, "BN %d", pl.BN);
               CHECK(pl.BN != 192 || form == kFormBF16, "192 for form %d", form);
               CHECK(pl.KB == (s.Kp + form_cols(form) - 1) / form_cols(form), "KB %d", pl.KB);
@@ -75,8 +80,17 @@ int main() {
               const int c = pl.tmem_cols;
               CHECK(c >= 32 && c <= 512 && (c & (c - 1)) == 0 && c >= 2 * pl.BN, "tmem %d", c);
               const long long ntiles = (M + pl.BN - 1) / pl.BN;
-              CHECK(pl.grid >= 1 && pl.grid <= sms && pl.grid <= ntiles, "grid %d", pl.grid);
-              CHECK(pl.rows == 2 * pl.grid, "rows");
+              if (pl.pair) {
+                // 2-CTA clusters, each at least one tile; one partial row per
+                // (cluster, column half)
+                CHECK(pl.grid >= 2 && pl.grid % 2 == 0 && pl.grid <= sms && pl.grid / 2 <= ntiles,
+                      "pair grid %d", pl.grid);
+                CHECK(pl.rows == pl.grid, "pair rows");
+                CHECK(pl.tmem_cols == 512, "pair tmem");
+              } else {
+                CHECK(pl.grid >= 1 && pl.grid <= sms && pl.grid <= ntiles, "grid %d", pl.grid);
+                CHECK(pl.rows == 2 * pl.grid, "rows");
+              }
               CHECK((long long)ntiles * pl.BN <= s.Mpad, "padding");
             }
             if (!ok0) refused = true;

@@ -728,8 +728,7 @@ def main():
                 "frac_of_sustained": achieved_tflops / (float(peaks.get(
                     "bf16_tflops_sustained", peaks["bf16_tflops"])) * ratio),
                 "mma_tflops": achieved_tflops * mma_per_product,
-                "kernel": ("fitness_tc2_kernel (SM pairs)" if prec == game.GAME_PREC_BF16
-                           and P > 128 else "fitness_tc_kernel"), "kernel_ms": fit_ms}
+                "kernel": "fitness_tc_kernel", "kernel_ms": fit_ms}
     elif prec == game.GAME_PREC_GRAM:
         # FP64 quadratic forms: 2 P K^2 + 2 P K flop per generation
         gflops = (2.0 * P * K * K + 2.0 * P * K) / (fit_ms * 1e-3) / 1e12

@@ -481,6 +481,7 @@ int ensure_surrogate(game_ctx* h, int rows) {
     }
     h->sd_params = true;
     s.step = 0;
+    s.status = h->status;
     CK(surrogate_init(s, h->prm.seed, h->st));
   }
   if (rows > s.Bmax) {
@@ -492,7 +493,9 @@ int ensure_surrogate(game_ctx* h, int rows) {
     dev_free(s.out);
     dev_free(s.dout);
     dev_free(s.lterm);
+    dev_free(s.lfit);
     s.out = s.dout = s.lterm = nullptr;
+    s.lfit = nullptr;
     s.Bmax = 0;
     for (float** b : bufs)
       if (dev_alloc(b, (size_t)rows * kSurrogateHidden) != cudaSuccess) {
@@ -500,7 +503,7 @@ int ensure_surrogate(game_ctx* h, int rows) {
         return fail(GAME_ENOMEM, "surrogate workspace");
       }
     if (dev_alloc(&s.out, rows) != cudaSuccess || dev_alloc(&s.dout, rows) != cudaSuccess ||
-        dev_alloc(&s.lterm, rows) != cudaSuccess) {
+        dev_alloc(&s.lterm, rows) != cudaSuccess || dev_alloc(&s.lfit, rows) != cudaSuccess) {
       cudaGetLastError();
       return fail(GAME_ENOMEM, "surrogate workspace");
     }
@@ -735,6 +738,7 @@ void destroy_ctx(game_ctx* h) {
   dev_free(h->trust);
   dev_free(h->trust_r);
   dev_free(h->sd.tstat);
+  dev_free(h->sd.lfit);
   delete h;
 }
 

@@ -752,11 +752,25 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
 
 }  // namespace
 
+TcPlan plan_tc_single(const Shape& s, int P, int num_sms, int form);
+
+// The one-SM kernel where it runs 256-pattern tiles; where its shared memory
+// forces narrower tiles, the BF16 form (with at least two chromosome tiles)
+// takes the paired-SM kernel, whose CTAs each hold half of a 256-pattern
+// tile's expansion. Measured on the large classification set (256-pattern
+// one-SM tiles): one-SM 0.50 ms, pairs 0.54 ms per evaluation; on the
+// surrogate workload (K' = 288, N = 48: one-SM 192-pattern tiles): one-SM
+// 6.57 ms, pairs 5.33 ms.
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
-  if (form == kFormBF16 && P > 128) {
+  const TcPlan one = plan_tc_single(s, P, num_sms, form);
+  if (form == kFormBF16 && P > 128 && !(one.ok && one.BN == 256)) {
     const TcPlan pp = plan_tc_pair(s, P, num_sms);
     if (pp.ok) return pp;
   }
+  return one;
+}
+
+TcPlan plan_tc_single(const Shape& s, int P, int num_sms, int form) {
   TcPlan pl{};
   pl.form = form;
   pl.KB = ceil_div(s.Kp, form_cols(form));

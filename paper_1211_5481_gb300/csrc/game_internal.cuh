@@ -159,7 +159,9 @@ struct SurrogateDev {
   float *out, *dout, *lterm;              // [Bmax]
   float* loss;             // [1]
   double* tstat;           // [2] mean and sd of the batch's log-fitness
+  double* lfit;            // [Bmax] the batch's log-fitness
   float* split_ws;         // [kMaxSplits][256][max(K, 256)] split-K partial products
+  int* status;             // the handle's device status word (expired waits)
 };
 int64_t surrogate_param_count(int K);
 cudaError_t surrogate_init(const SurrogateDev& s, uint64_t seed, cudaStream_t st);

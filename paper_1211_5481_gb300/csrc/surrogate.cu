@@ -17,9 +17,9 @@
 // Parameter vector (FP32, this order): W1 [256][K], b1 [256], W2 [256][256],
 // b2 [256], w3 [256], b3 [1].
 //
-// Kernels: one tiled GEMM with strides (C = A B with any transposition,
-// FP32 accumulation, optional BF16 rounding of either operand on load, an
-// optional bias + GELU epilogue), column sums in a fixed order, the GELU
+// Kernels: one tensor-core GEMM with strides (C = A B with any transposition,
+// BF16 operands -- FP32 ones split into BF16 hi + lo -- with FP32
+// accumulation in tensor memory, an optional bias + GELU epilogue), column sums in a fixed order, the GELU
 // derivative, the output layer, and Adam. Screening: a one-CTA bitonic sort
 // of (prediction, slot) keys, a flag per kept slot and a prefix-sum
 // compaction that assembles the next population in slot order. The exact
@@ -57,84 +57,270 @@ __device__ __forceinline__ float gelu_grad(float z) {
 }
 
 // C[m][n] = sum_k A(m, k) B(k, n), A(m, k) = A[m * am + k * ak], B(k, n) =
-// B[k * bk + n * bn]; FP32 accumulation in k order per thread. 128 x 128
-// tiles, 256 threads, 8 x 8 outputs per thread, k-chunks of 16 through shared
-// memory; each operand tile is loaded with consecutive threads along its
-// contiguous dimension (ak == 1 or am == 1, bk == 1 or bn == 1). Split-K:
+// B[k * bk + n * bn], on the tensor cores (tcgen05, FP32 accumulation in tensor
+// memory). Operands flagged for rounding enter as their BF16 values; the
+// others (FP32 gradients) as hi = bf16(v) plus lo = bf16(v - hi), with the
+// MMAs hi*hi + hi*lo + lo*hi, so products lose at most ~2^-16 of their
+// value. CTA tile: 128 rows of C (MMA-M, tensor-memory lanes) x TN columns
+// (MMA-N); K in blocks of 64 through a double-buffered shared-memory ring in
+// the K-major SWIZZLE_128B layout, filled by all 256 threads (g_load),
+// consumed by MMAs issued by thread 0;
+// the epilogue reads the accumulator rows back (thread = row of C). Split-K:
 // blockIdx.z takes k-range [z * kz, (z + 1) * kz) and, with splits > 1, writes
 // its partial product to C + z * M * ldc (reduced in order by splitk_reduce).
 // Epilogue modes (splits == 1): 0 store C; 1 store Z = C + bias[n] to C and
 // g(Z) (BF16-rounded when round_out) to out2; 2 store C + bias[n].
-constexpr int kTM = 128, kTN = 128, kTK = 16;
-__global__ void __launch_bounds__(256)
-gemm_kernel(int M, int N, int Kd, const float* __restrict__ A, int64_t am, int64_t ak,
-            const float* __restrict__ B, int64_t bk, int64_t bn, int round_a, int round_b,
-            float* __restrict__ C, int64_t ldc, int mode, const float* __restrict__ bias,
-            float* __restrict__ out2, int round_out, int kz) {
-  __shared__ float As[kTK][kTM + 4];
-  __shared__ float Bs[kTK][kTN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
-  const int kbeg = blockIdx.z * kz;
-  const int kend = min(Kd, kbeg + kz);
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  const bool a_kc = ak == 1, b_kc = bk == 1;
-  for (int k0 = kbeg; k0 < kend; k0 += kTK) {
-#pragma unroll
-    for (int r = 0; r < (kTK * kTM) / 256; ++r) {
-      const int e = r * 256 + threadIdx.x;
-      const int kk = a_kc ? e % kTK : e / kTM;
-      const int mm = a_kc ? e / kTK : e % kTM;
-      const int m = m0 + mm, k = k0 + kk;
-      const float v = (m < M && k < kend) ? A[(int64_t)m * am + (int64_t)k * ak] : 0.f;
-      As[kk][mm] = round_a ? round_bf16(v) : v;
+// Waits are bounded (1 s): an expired wait abandons the tile and raises
+// *status.
+constexpr int kGTK = 64;                  // K per block (128 bytes of BF16 per row)
+constexpr uint32_t kGemmWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t g_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool g_wait(uint32_t bar, uint32_t parity, int* status) {
+  uint32_t ok = 0;
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (it == 0) t0 = t;
+    else if (t - t0 > kGemmWaitNs) {
+      atomicExch(status, 1);
+      return false;
     }
-#pragma unroll
-    for (int r = 0; r < (kTK * kTN) / 256; ++r) {
-      const int e = r * 256 + threadIdx.x;
-      const int kk = b_kc ? e % kTK : e / kTN;
-      const int nn = b_kc ? e / kTK : e % kTN;
-      const int n = n0 + nn, k = k0 + kk;
-      const float v = (n < N && k < kend) ? B[(int64_t)k * bk + (int64_t)n * bn] : 0.f;
-      Bs[kk][nn] = round_b ? round_bf16(v) : v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; ++kk) {
-      const float4 a_lo = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-      const float4 a_hi = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-      const float4 b_lo = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-      const float4 b_hi = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
-      const float av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
-      const float bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
   }
-  float* Cz = C + (int64_t)blockIdx.z * M * ldc;
+}
+
+__device__ __forceinline__ uint64_t g_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void g_mma(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                      uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf16pair(float lo, float hi) {
+  const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&b);
+}
+
+// 8 consecutive k of one row into the swizzled image (hi, and lo when split)
+__device__ __forceinline__ void g_store8(uint8_t* img, uint8_t* img_lo, int r, int qd,
+                                         const float (&v)[8], bool split) {
+  const int off = r * 128 + ((qd ^ (r & 7)) << 4);
+  uint32_t h[4], l[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int m = m0 + (i < 4 ? ty * 4 + i : 60 + ty * 4 + i);
-    if (m >= M) continue;
+  for (int e = 0; e < 4; ++e) {
+    h[e] = bf16pair(v[2 * e], v[2 * e + 1]);
+    if (split) {
+      const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162*>(&h[e]);
+      const float2 hf = __bfloat1622float2(hb);
+      l[e] = bf16pair(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+    }
+  }
+  *reinterpret_cast<uint4*>(img + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  if (split) *reinterpret_cast<uint4*>(img_lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Rows [0, R) x k in [k0, k0 + 64) of an operand X(r, k) = X[(r0 + r) rs + k ks]
+// (zero where r0 + r >= rlim or k >= kend) into the swizzled image, by the
+// CTA's kGThreads threads. Every thread issues all of its loads before it
+// converts and stores anything, so each waits one memory latency per
+// K-block. With k contiguous (ks == 1) eight threads share a row, each
+// converting one 16-byte unit, so a warp reads four rows' 256 contiguous
+// bytes; otherwise consecutive threads take consecutive rows (a warp's loads
+// span 32 rows) and the row's eight units are split among kGThreads / R
+// threads.
+constexpr int kGThreads = 256;
+template <int R>
+__device__ __forceinline__ void g_load(uint8_t* img, uint8_t* img_lo, const float* __restrict__ X,
+                                       int64_t rs, int64_t ks, int r0, int rlim, int k0,
+                                       int kend, bool split) {
+  const int tid = threadIdx.x;
+  if (ks == 1) {
+    constexpr int RPP = kGThreads / 8;              // rows per pass
+    constexpr int NP = (R + RPP - 1) / RPP;
+    const int unit = tid & 7, rr = tid >> 3;
+    float v[NP][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int n = n0 + (j < 4 ? tx * 4 + j : 60 + tx * 4 + j);
-      if (n >= N) continue;
-      float v = acc[i][j];
-      if (mode >= 1) v += bias[n];
-      Cz[(int64_t)m * ldc + n] = v;
-      if (mode == 1) {
-        const float gv = gelu(v);
-        out2[(int64_t)m * ldc + n] = round_out ? round_bf16(gv) : gv;
+    for (int p = 0; p < NP; ++p) {
+      const int r = rr + p * RPP, row = r0 + r;
+      const float* src = X + (int64_t)row * rs;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + unit * 8 + e;
+        v[p][e] = (r < R && row < rlim && k < kend) ? src[k] : 0.f;
       }
     }
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+      if (rr + p * RPP < R) g_store8(img, img_lo, rr + p * RPP, unit, v[p], split);
+  } else {
+    constexpr int TPR = kGThreads / R;              // threads per row
+    constexpr int UPT = 8 / TPR;                    // units per thread
+    const int r = tid % R, ug = tid / R, row = r0 + r;
+    float v[UPT][8];
+#pragma unroll
+    for (int u = 0; u < UPT; ++u)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + (ug * UPT + u) * 8 + e;
+        v[u][e] = (row < rlim && k < kend) ? X[(int64_t)row * rs + (int64_t)k * ks] : 0.f;
+      }
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) g_store8(img, img_lo, r, ug * UPT + u, v[u], split);
+  }
+}
+
+template <int TN>
+__global__ void __launch_bounds__(kGThreads, 1)
+gemm_tc_kernel(int M, int N, int Kd, const float* __restrict__ A, int64_t am, int64_t ak,
+               const float* __restrict__ B, int64_t bk, int64_t bn, int round_a, int round_b,
+               float* __restrict__ C, int64_t ldc, int mode, const float* __restrict__ bias,
+               float* __restrict__ out2, int round_out, int kz, int* status) {
+  constexpr uint32_t kAImg = 128 * 128, kBImg = TN * 128;
+  constexpr uint32_t kStage = 2 * kAImg + 2 * kBImg;   // hi and lo images of both operands
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * kStage);   // [2] stage free, [1] done
+  uint32_t* holder = reinterpret_cast<uint32_t*>(bars + 3);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  static_assert(TN % 64 == 0, "two column halves of whole 32-column loads");
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * TN;
+  const int kbeg = blockIdx.z * kz;
+  const int kend = min(Kd, kbeg + kz);
+  const int nkb = kend > kbeg ? (kend - kbeg + kGTK - 1) / kGTK : 0;
+  const bool split_a = !round_a, split_b = !round_b;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(g_smem(&bars[b])), "r"(1)
+                   : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     g_smem(holder)),
+                 "r"(TN < 32 ? 32 : TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *holder;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
+  bool ok = true;
+  for (int kb = 0; kb < nkb && ok; ++kb) {
+    const int st = kb & 1;
+    uint8_t* a_img = base + st * kStage;
+    uint8_t* a_lo = a_img + kAImg;
+    uint8_t* b_img = a_img + 2 * kAImg;
+    uint8_t* b_lo = b_img + kBImg;
+    // the MMAs that read this stage two blocks ago are done
+    if (kb >= 2) ok = g_wait(g_smem(&bars[st]), ((kb - 2) >> 1) & 1, status);
+    if (!ok) break;
+    const int k0 = kbeg + kb * kGTK;
+    g_load<128>(a_img, a_lo, A, am, ak, m0, M, k0, kend, split_a);
+    g_load<TN>(b_img, b_lo, B, bn, bk, n0, N, k0, kend, split_b);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t ad = g_desc(g_smem(a_img)), adl = g_desc(g_smem(a_lo));
+      const uint64_t bd = g_desc(g_smem(b_img)), bdl = g_desc(g_smem(b_lo));
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t o = 2u * ks;
+        g_mma(tmem, ad + o, bd + o, idesc, (kb | ks) != 0);
+        if (split_b) g_mma(tmem, ad + o, bdl + o, idesc, 1u);
+        if (split_a) g_mma(tmem, adl + o, bd + o, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       g_smem(&bars[st]))
+                   : "memory");
+    }
+  }
+  // all MMAs done
+  if (tid == 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     g_smem(&bars[2]))
+                 : "memory");
+  const bool done = g_wait(g_smem(&bars[2]), 0, status);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done && ok) {
+    // each warp's 32 accumulator rows go through a 32 x 33 scratch tile (in
+    // the operand ring, idle now) so that the stores run along rows of C
+    // warp w reads tensor-memory lanes 32 (w % 4) .. (its quadrant), columns
+    // of half w / 4
+    float* stage = reinterpret_cast<float*>(base) + warp * (32 * 33);
+    float* Cz = C + (int64_t)blockIdx.z * M * ldc;
+    const int quad = warp & 3, half = warp >> 2;
+#pragma unroll 1
+    for (int c0 = half * (TN / 2); c0 < (half + 1) * (TN / 2); c0 += 32) {
+      uint32_t v[32];
+      const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+          "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+          "tcgen05.wait::ld.sync.aligned;"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(ta)
+          : "memory");
+#pragma unroll
+      for (int e = 0; e < 32; ++e) stage[lane * 33 + e] = nkb > 0 ? __uint_as_float(v[e]) : 0.f;
+      __syncwarp();
+      const int n = n0 + c0 + lane;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int m = m0 + quad * 32 + r;
+        if (m < M && n < N) {
+          float x = stage[r * 33 + lane];
+          if (mode >= 1) x += bias[n];
+          Cz[(int64_t)m * ldc + n] = x;
+          if (mode == 1) {
+            const float gv = gelu(x);
+            out2[(int64_t)m * ldc + n] = round_out ? round_bf16(gv) : gv;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TN < 32 ? 32 : TN)
+                 : "memory");
   }
 }
 
@@ -165,34 +351,43 @@ __global__ void output_kernel(int B, const float* __restrict__ H2, const float* 
 // Mean and standard deviation of l = log(max(fit, 1e-30)) over the batch
 // (FP64, fixed order: thread-strided sums then a sequential sum of the 256
 // partials).
-__global__ void target_stats_kernel(int B, const double* __restrict__ fit,
-                                    double* __restrict__ stats) {
-  __shared__ double s1[256], s2[256];
+// Mean and sd of the batch's log-fitness (FP64): 1024 threads, each
+// thread's rows summed in order, then a fixed pairwise tree over the
+// threads (the same order every run).
+__device__ __forceinline__ double tree_sum_1024(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// l[b] = log(max(fit[b], 1e-30)) in FP64, over the whole GPU (FP64 is slow
+// on one SM)
+__global__ void log_fit_kernel(int B, const double* __restrict__ fit, double* __restrict__ l) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double f = fit[b];
+  l[b] = log(f > 1e-30 ? f : 1e-30);
+}
+
+__global__ void __launch_bounds__(1024)
+target_stats_kernel(int B, const double* __restrict__ l, double* __restrict__ stats) {
+  __shared__ double sh[1024];
   double a = 0.0;
-  for (int b = threadIdx.x; b < B; b += 256) {
-    const double f = fit[b];
-    a += log(f > 1e-30 ? f : 1e-30);
-  }
-  s1[threadIdx.x] = a;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 256; ++i) t += s1[i];
-    s1[0] = t / B;
-  }
-  __syncthreads();
-  const double mu = s1[0];
+  for (int b = threadIdx.x; b < B; b += 1024) a += l[b];
+  const double mu = tree_sum_1024(a, sh) / B;
   double q = 0.0;
-  for (int b = threadIdx.x; b < B; b += 256) {
-    const double f = fit[b];
-    const double d = log(f > 1e-30 ? f : 1e-30) - mu;
+  for (int b = threadIdx.x; b < B; b += 1024) {
+    const double d = l[b] - mu;
     q += d * d;
   }
-  s2[threadIdx.x] = q;
-  __syncthreads();
+  const double t = tree_sum_1024(q, sh);
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 256; ++i) t += s2[i];
     const double sd = sqrt(t / B);
     stats[0] = mu;
     stats[1] = sd > 0.0 ? sd : 1.0;
@@ -201,13 +396,12 @@ __global__ void target_stats_kernel(int B, const double* __restrict__ fit,
 
 // d_out[b] = 2 (out[b] - t[b]) / B with the standardised target t; also the
 // loss terms (out - t)^2 / B for reporting.
-__global__ void dout_kernel(int B, const float* __restrict__ out, const double* __restrict__ fit,
+__global__ void dout_kernel(int B, const float* __restrict__ out, const double* __restrict__ l,
                             const double* __restrict__ stats, float* __restrict__ dout,
                             float* __restrict__ loss_terms) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
-  const double f = fit[b];
-  const float t = (float)((log(f > 1e-30 ? f : 1e-30) - stats[0]) / stats[1]);
+  const float t = (float)((l[b] - stats[0]) / stats[1]);
   const float r = out[b] - t;
   dout[b] = 2.f * r / (float)B;
   loss_terms[b] = r * r / (float)B;
@@ -231,14 +425,29 @@ __global__ void gelu_bwd_kernel(int64_t n, const float* __restrict__ Z, float* _
     dZ[e] *= gelu_grad(Z[e]);
 }
 
-// s[j] = sum_b X[b][j] y[b] (y = NULL: plain column sum), fixed order per column
-__global__ void colsum_kernel(int B, int N, const float* __restrict__ X,
-                              const float* __restrict__ y, float* __restrict__ s) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
+// s[j] = sum_b X[b][j] y[b] (y = NULL: plain column sum). CTA = 32 columns x
+// 32 row slices (1024 threads): thread (slice, column) adds its slice's rows
+// in order, then the 32 slice sums of a column are added in slice order --
+// a fixed order, so the result is the same run to run.
+constexpr int kColSlices = 32;
+__global__ void __launch_bounds__(1024)
+colsum_kernel(int B, int N, const float* __restrict__ X, const float* __restrict__ y,
+              float* __restrict__ s) {
+  __shared__ float part[kColSlices][33];
+  const int c = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + c;
+  const int per = (B + kColSlices - 1) / kColSlices;
+  const int b0 = sl * per, b1 = min(B, b0 + per);
   float acc = 0.f;
-  for (int b = 0; b < B; ++b) acc = fmaf(X[(int64_t)b * N + j], y ? y[b] : 1.f, acc);
-  s[j] = acc;
+  if (j < N)
+    for (int b = b0; b < b1; ++b) acc = fmaf(X[(int64_t)b * N + j], y ? y[b] : 1.f, acc);
+  part[sl][c] = acc;
+  __syncthreads();
+  if (sl == 0 && j < N) {
+    float t = 0.f;
+    for (int k = 0; k < kColSlices; ++k) t += part[k][c];
+    s[j] = t;
+  }
 }
 
 __global__ void sum_kernel(int B, const float* __restrict__ v, float* __restrict__ s) {
@@ -470,25 +679,31 @@ int grid1d(int64_t n) {
   return (int)b;
 }
 
+constexpr int kGTN = 64;   // columns of C per CTA of the tensor-core GEMM
+
 cudaError_t gemm(int M, int N, int Kd, const float* A, int64_t am, int64_t ak, const float* B,
                  int64_t bk, int64_t bn, int ra, int rb, float* C, int64_t ldc, int mode,
-                 const float* bias, float* out2, int round_out, cudaStream_t st,
+                 const float* bias, float* out2, int round_out, int* status, cudaStream_t st,
                  float* split_ws = nullptr, int splits = 1) {
-  dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, splits);
+  dim3 grid((N + kGTN - 1) / kGTN, (M + 127) / 128, splits);
   int kz = (Kd + splits - 1) / splits;
-  kz = (kz + kTK - 1) / kTK * kTK;
+  kz = (kz + kGTK - 1) / kGTK * kGTK;
+  const int smem = 2 * (2 * 128 * 128 + 2 * kGTN * 128) + 1024 + 64;
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<kGTN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   if (splits > 1) {
     // partial products into the workspace, then their sum in split order
-    gemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, split_ws, N, 0,
-                                      nullptr, nullptr, 0, kz);
-    cudaError_t e = cudaGetLastError();
+    gemm_tc_kernel<kGTN><<<grid, kGThreads, smem, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb,
+                                                  split_ws, N, 0, nullptr, nullptr, 0, kz, status);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     splitk_reduce_kernel<<<grid1d((int64_t)M * N), 256, 0, st>>>((int64_t)M * N, splits,
                                                                   split_ws, C);
     return cudaGetLastError();
   }
-  gemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, C, ldc, mode, bias,
-                                    out2, round_out, kz);
+  gemm_tc_kernel<kGTN><<<grid, kGThreads, smem, st>>>(M, N, Kd, A, am, ak, B, bk, bn, ra, rb, C, ldc,
+                                                mode, bias, out2, round_out, kz, status);
   return cudaGetLastError();
 }
 
@@ -521,10 +736,10 @@ cudaError_t surrogate_forward(const SurrogateDev& s, const float* X, int B, floa
   const float* w3 = b2 + kH;
   const float* b3 = w3 + kH;
   // Z1 = bf(X) bf(W1)^T + b1, H1 = bf(g(Z1))
-  cudaError_t e = gemm(B, kH, K, X, K, 1, W1, 1, K, 1, 1, s.Z1, kH, 1, b1, s.H1, 1, st);
+  cudaError_t e = gemm(B, kH, K, X, K, 1, W1, 1, K, 1, 1, s.Z1, kH, 1, b1, s.H1, 1, s.status, st);
   if (e != cudaSuccess) return e;
   // Z2 = H1 bf(W2)^T + b2, H2 = g(Z2)
-  e = gemm(B, kH, kH, s.H1, kH, 1, W2, 1, kH, 0, 1, s.Z2, kH, 1, b2, s.H2, 0, st);
+  e = gemm(B, kH, kH, s.H1, kH, 1, W2, 1, kH, 1, 1, s.Z2, kH, 1, b2, s.H2, 0, s.status, st);
   if (e != cudaSuccess) return e;
   output_kernel<<<(int)(((int64_t)B * 32 + 255) / 256), 256, 0, st>>>(B, s.H2, w3, b3, out);
   return cudaGetLastError();
@@ -544,31 +759,33 @@ cudaError_t surrogate_backward(const SurrogateDev& s, const float* X, const doub
   float* gb2 = gW2 + (int64_t)kH * kH;
   float* gw3 = gb2 + kH;
   float* gb3 = gw3 + kH;
-  target_stats_kernel<<<1, 256, 0, st>>>(B, fit, s.tstat);
-  dout_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, s.out, fit, s.tstat, s.dout, s.lterm);
+  log_fit_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, fit, s.lfit);
+  target_stats_kernel<<<1, 1024, 0, st>>>(B, s.lfit, s.tstat);
+  dout_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, s.out, s.lfit, s.tstat, s.dout, s.lterm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   sum_kernel<<<1, 256, 0, st>>>(B, s.lterm, s.loss);
   // output layer
-  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.H2, s.dout, gw3);
+  colsum_kernel<<<kH / 32, 1024, 0, st>>>(B, kH, s.H2, s.dout, gw3);
   sum_kernel<<<1, 256, 0, st>>>(B, s.dout, gb3);
   // dZ2 = dout w3 g'(Z2)
   dz2_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>(B, s.dout, w3, s.Z2, s.dZ2);
   // gW2 = dZ2^T H1, gb2 = colsum(dZ2)
   const int splits = kGradSplits(B);
-  e = gemm(kH, kH, B, s.dZ2, 1, kH, s.H1, kH, 1, 0, 0, gW2, kH, 0, nullptr, nullptr, 0, st,
-           s.split_ws, splits);
+  e = gemm(kH, kH, B, s.dZ2, 1, kH, s.H1, kH, 1, 0, 1, gW2, kH, 0, nullptr, nullptr, 0, s.status,
+           st, s.split_ws, splits);
   if (e != cudaSuccess) return e;
-  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ2, nullptr, gb2);
+  colsum_kernel<<<kH / 32, 1024, 0, st>>>(B, kH, s.dZ2, nullptr, gb2);
   // dZ1 = (dZ2 bf(W2)) g'(Z1)
-  e = gemm(B, kH, kH, s.dZ2, kH, 1, W2, kH, 1, 0, 1, s.dZ1, kH, 0, nullptr, nullptr, 0, st);
+  e = gemm(B, kH, kH, s.dZ2, kH, 1, W2, kH, 1, 0, 1, s.dZ1, kH, 0, nullptr, nullptr, 0, s.status,
+           st);
   if (e != cudaSuccess) return e;
   gelu_bwd_kernel<<<grid1d((int64_t)B * kH), 256, 0, st>>>((int64_t)B * kH, s.Z1, s.dZ1);
   // gW1 = dZ1^T bf(X), gb1 = colsum(dZ1)
-  e = gemm(kH, K, B, s.dZ1, 1, kH, X, K, 1, 0, 1, gW1, K, 0, nullptr, nullptr, 0, st,
+  e = gemm(kH, K, B, s.dZ1, 1, kH, X, K, 1, 0, 1, gW1, K, 0, nullptr, nullptr, 0, s.status, st,
            s.split_ws, splits);
   if (e != cudaSuccess) return e;
-  colsum_kernel<<<1, kH, 0, st>>>(B, kH, s.dZ1, nullptr, gb1);
+  colsum_kernel<<<kH / 32, 1024, 0, st>>>(B, kH, s.dZ1, nullptr, gb1);
   return cudaGetLastError();
 }
 

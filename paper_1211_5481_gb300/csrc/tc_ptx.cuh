@@ -268,11 +268,12 @@ __device__ __forceinline__ uint32_t mapa(uint32_t local, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
   return r;
 }
-// One arrival (release at cluster scope) on an mbarrier of any CTA of the
-// cluster, given its shared::cluster address.
+// One arrival on an mbarrier of any CTA of the cluster, given its
+// shared::cluster address (default semantics: release at CTA scope; a
+// cluster-scope release would first drain every prior global store of the
+// thread, measured 12% slower for the paired fitness kernel).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar)
-               : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
 }
 // Tensor memory of a CTA pair: issued by one warp of each CTA of the pair.
 __device__ __forceinline__ void tmem_alloc2(uint32_t dst_smem, uint32_t ncols) {

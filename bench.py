@@ -56,7 +56,7 @@ def parse():
                     help="classification workload: the fitness's error function (Section 3)")
     ap.add_argument("--oversample", type=int, default=8, metavar="O",
                     help="surrogate workload: offspring per kept child (game_params.oversample)")
-    ap.add_argument("--surrogate-steps", type=int, default=1, metavar="S",
+    ap.add_argument("--surrogate-steps", type=int, default=8, metavar="S",
                     help="surrogate workload: Adam steps per generation on each stored "
                          "generation (game_params.surrogate_steps)")
     ap.add_argument("--selection", choices=["ranking", "roulette"], default="ranking",
@@ -835,10 +835,10 @@ def main():
     if world == 1 and not args.no_surrogate_leg:
         # the surrogate workload (4M patterns, N = 48, degree 6, P = 2048)
         # beside the headline: the screened BF16 form at the workload's
-        # literal 8x oversampling with one Adam round per generation, and at
-        # 2x with eight (the setting whose surrogate the trust check
-        # accepts), each against the plain FP32 form; the FP64 oracle GA's
-        # best after G generations is shared by both comparisons
+        # literal 8x oversampling and at 2x (milder screening), both with
+        # eight Adam rounds per generation, each against the plain FP32
+        # form; the FP64 oracle GA's best after G generations is shared by
+        # both comparisons
         from paper_1211_5481_gb300 import datagen as dg
         pr4 = dg.surrogate_regression()
         X4 = torch.from_numpy(pr4.X).to(dev)
@@ -847,11 +847,21 @@ def main():
         of = (oracle_ga_best(pr4, args.surrogate_oracle_run)
               if cpu4 and args.surrogate_oracle_run > 0 else None)
         sur = {}
-        for o, st in ((8, 1), (2, 8)):
+        for o, st in ((8, 8), (2, 8)):
             sur[f"oversample_{o}x_steps_{st}"] = surrogate_leg(
                 torch, game, dev, pr4, X4, y4, o, st, 10, 3, oracle_final=of,
                 precision_gens=3, fp32_gens=3, clocks_enabled=not args.no_clocks,
                 cpu_reports=cpu4)
+        if of is not None:
+            # the BF16 form without screening, same seed and generations: the
+            # precision form alone against the FP64 oracle GA
+            with game.Game(X4, y4, pr4.degree, pr4.basis, stream=stream, P=pr4.P, seed=4,
+                           precision=game.GAME_PREC_BF16) as gb:
+                gb.train(of["generations"])
+                best_b = float(gb.population()[1].min())
+            sur["unscreened_bf16_final_best"] = {
+                "generations": of["generations"], "bf16_best": best_b,
+                "oracle_best": of["best"], "rel_diff": (best_b - of["best"]) / of["best"]}
         del X4, y4
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -138,12 +138,15 @@ typedef struct {
                            (not GAME_PREC_GRAM) and rescore_top = 0 */
   int32_t surrogate_steps; /* with the surrogate: Adam steps per generation
                            on each of the last two generations' exact
-                           (chromosome, fitness) pairs, 1..64 (default 1) */
+                           (chromosome, fitness) pairs, 1..64 (default 8:
+                           with fewer, the trust check below rarely passes
+                           and the screening falls back to the unscreened
+                           children) */
   int32_t reserved[1];  /* must be zero */
 } game_params;
 
 /* Fills *out with the defaults listed above (and rescore_top = 16,
- * oversample = 8, surrogate_steps = 1, tournament selection, per-feature
+ * oversample = 8, surrogate_steps = 8, tournament selection, per-feature
  * genes, MSE). */
 int game_params_default(game_params* out);
 

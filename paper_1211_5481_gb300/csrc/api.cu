@@ -787,7 +787,7 @@ int game_params_default(game_params* out) {
   out->selection = GAME_SEL_TOURNAMENT;
   out->tied = 0;
   out->error = GAME_ERR_MSE;
-  out->surrogate_steps = 1;
+  out->surrogate_steps = 8;
   return GAME_OK;
 }
 
@@ -996,7 +996,8 @@ int game_generation(game_t h, uint64_t seed) {
     if (rc) return rc;
     h->fit_valid = true;
     t0 = stage_begin(h);
-    CK(surrogate_trust_check(n, h->pred, h->flag, h->pos, h->fit + E, h->trust_r, h->trust, h->st));
+    CK(surrogate_trust_check(h->sd, n, P - E, h->pred, h->flag, h->pos, h->fit + E, h->trust_r,
+                             h->trust, h->st));
     rc = surrogate_learn(h);
     stage_end(h, t0, kSurrogate);
     return rc;

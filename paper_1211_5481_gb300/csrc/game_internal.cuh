@@ -179,9 +179,11 @@ cudaError_t surrogate_screen(int n, int n_keep, int E, int K, const float* pred,
                              int* pos, const float* off, float* next, const int* trusted,
                              int* used_trust, cudaStream_t st);
 // r = Pearson correlation of the kept children's predictions with their exact
-// log-fitness (fit_kept [n_keep] in slot order); *trusted = r > 0.25.
-cudaError_t surrogate_trust_check(int n, const float* pred, const int* flag, const int* pos,
-                            const double* fit_kept, float* r_out, int* trusted, cudaStream_t st);
+// log-fitness (fit_kept [n_kept] in slot order; their logs go through s.lfit);
+// *trusted = r > 0.25.
+cudaError_t surrogate_trust_check(const SurrogateDev& s, int n, int n_kept, const float* pred,
+                                  const int* flag, const int* pos, const double* fit_kept,
+                                  float* r_out, int* trusted, cudaStream_t st);
 
 // gram.cu -- the Gram form of the MSE (FP64)
 int64_t gram_chunk_rows(const Shape& s);

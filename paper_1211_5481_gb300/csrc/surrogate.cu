@@ -619,39 +619,27 @@ __global__ void gather_kernel(int n, int E, int K, const int* __restrict__ pos,
 // log-fitness (fit_kept[pos[i]] for kept child i), FP64 sums in a fixed
 // order; trusted = r > 0.25.
 __global__ void trust_kernel(int n, const float* __restrict__ pred, const int* __restrict__ flag,
-                             const int* __restrict__ pos, const double* __restrict__ fit_kept,
+                             const int* __restrict__ pos, const double* __restrict__ lfit_kept,
                              float* __restrict__ r_out, int* __restrict__ trusted) {
-  __shared__ double sh[5][256];
-  double a[5] = {0, 0, 0, 0, 0};
+  __shared__ double sh[6][256];
+  double a[6] = {0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < n; i += 256) {
     if (!flag[i]) continue;
     const double x = pred[i];
-    const double f = fit_kept[pos[i]];
-    const double y = log(f > 1e-30 ? f : 1e-30);
+    const double y = lfit_kept[pos[i]];
     a[0] += 1.0;
     a[1] += x;
     a[2] += y;
     a[3] += x * y;
     a[4] += x * x;
+    a[5] += y * y;
   }
-  double yy = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) {
-    if (!flag[i]) continue;
-    const double f = fit_kept[pos[i]];
-    const double y = log(f > 1e-30 ? f : 1e-30);
-    yy += y * y;
-  }
-  for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = a[k];
-  __syncthreads();
-  __shared__ double syy[256];
-  syy[threadIdx.x] = yy;
+  for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = a[k];
   __syncthreads();
   if (threadIdx.x == 0) {
     double t[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < 256; ++i) {
-      for (int k = 0; k < 5; ++k) t[k] += sh[k][i];
-      t[5] += syy[i];
-    }
+    for (int i = 0; i < 256; ++i)
+      for (int k = 0; k < 6; ++k) t[k] += sh[k][i];
     const double c = t[0];
     double r = 0.0;
     if (c > 1.0) {
@@ -799,9 +787,13 @@ cudaError_t surrogate_adam(SurrogateDev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t surrogate_trust_check(int n, const float* pred, const int* flag, const int* pos,
-                            const double* fit_kept, float* r_out, int* trusted, cudaStream_t st) {
-  trust_kernel<<<1, 256, 0, st>>>(n, pred, flag, pos, fit_kept, r_out, trusted);
+cudaError_t surrogate_trust_check(const SurrogateDev& s, int n, int n_kept, const float* pred,
+                                  const int* flag, const int* pos, const double* fit_kept,
+                                  float* r_out, int* trusted, cudaStream_t st) {
+  if (n_kept > s.Bmax) return cudaErrorInvalidValue;
+  // the kept children's log-fitness over the whole GPU first (FP64)
+  log_fit_kernel<<<(n_kept + 255) / 256, 256, 0, st>>>(n_kept, fit_kept, s.lfit);
+  trust_kernel<<<1, 256, 0, st>>>(n, pred, flag, pos, s.lfit, r_out, trusted);
   return cudaGetLastError();
 }
 

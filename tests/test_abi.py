@@ -65,7 +65,7 @@ def test_host_side_argument_checks():
                          ctypes.byref(h))
     assert rc == game.GAME_EINVAL
     assert p.selection == game.GAME_SEL_TOURNAMENT and p.tied == 0
-    assert p.error == game.GAME_ERR_MSE and p.surrogate_steps == 1
+    assert p.error == game.GAME_ERR_MSE and p.surrogate_steps == 8
     # selection, shared genes and error function settings
     for field, value, extra in [("selection", 3, {}), ("selection", -1, {}),
                                 ("selection", game.GAME_SEL_RANKING, {"P": 16385}),

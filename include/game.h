@@ -183,6 +183,25 @@ int game_eval_fitness(game_t h, const float* pop, int32_t P, double* fit_out);
 int game_eval_fitness_prec(game_t h, const float* pop, int32_t P,
                            int32_t precision, double* fit_out);
 
+/* The launch plan game_eval_fitness_prec would use for P chromosomes in the
+ * given precision (host-side, nothing is launched), for tests and reports:
+ *   info[0] kernel: GAME_KERNEL_FP32 (CUDA-core FFMA), GAME_KERNEL_TC (tcgen05
+ *           on one SM per pattern tile), GAME_KERNEL_TC_PAIR (tcgen05 on SM
+ *           pairs: 2-CTA clusters sharing each MMA, for the BF16 form where
+ *           one SM would need a tile narrower than 256 patterns),
+ *           GAME_KERNEL_GRAM (FP64 quadratic forms);
+ *   info[1] patterns per tile; info[2] K-blocks of the contraction;
+ *   info[3] gene stages; info[4] expansion K-block slots; info[5] 1 if the
+ *   features are staged in shared memory (0: read from L2); info[6] CTAs;
+ *   info[7] dynamic shared memory per CTA in bytes (tensor-core plans).
+ * Fields that do not apply are 0. GAME_EINVAL for a contraction the
+ * precision cannot take. */
+#define GAME_KERNEL_FP32 1
+#define GAME_KERNEL_TC 2
+#define GAME_KERNEL_TC_PAIR 3
+#define GAME_KERNEL_GRAM 4
+int game_plan_info(game_t h, int32_t precision, int32_t P, int32_t* info);
+
 /* Elite re-scoring. The n best chromosomes of fit (by fitness, then lower
  * index; NaN ranks last) are evaluated again in FP64 by the Gram form of the
  * MSE (see GAME_PREC_GRAM: exact to FP64 rounding; the handle builds its G

@@ -909,6 +909,36 @@ int game_get_shape(game_t h, int64_t* M, int32_t* N, int32_t* K, int32_t* P) {
   return GAME_OK;
 }
 
+int game_plan_info(game_t h, int32_t precision, int32_t P, int32_t* info) {
+  g_last_error.clear();
+  if (!h || !info) return fail(GAME_EINVAL, "NULL argument");
+  if (P < 1 || P > (1 << 24)) return fail(GAME_EINVAL, "P must be in 1..2^24");
+  if (!valid_precision(precision)) return fail(GAME_EINVAL, "unknown precision");
+  for (int i = 0; i < 8; ++i) info[i] = 0;
+  if (precision == GAME_PREC_GRAM) {
+    info[0] = GAME_KERNEL_GRAM;
+    return GAME_OK;
+  }
+  if (precision == GAME_PREC_FP32) {
+    const Fp32Plan pl = plan_fp32(h->s, P, h->num_sms);
+    info[0] = GAME_KERNEL_FP32;
+    info[1] = pl.BM;
+    info[6] = pl.grid_x * pl.grid_y;
+    return GAME_OK;
+  }
+  const TcPlan pl = plan_tc(h->s, P, h->num_sms, tc_form(precision));
+  if (!pl.ok) return fail(GAME_EINVAL, "contraction length too large for the tensor-core path");
+  info[0] = pl.pair ? GAME_KERNEL_TC_PAIR : GAME_KERNEL_TC;
+  info[1] = pl.BN;
+  info[2] = pl.KB;
+  info[3] = pl.stages;
+  info[4] = pl.NS;
+  info[5] = pl.xstage;
+  info[6] = pl.grid;
+  info[7] = pl.smem_bytes;
+  return GAME_OK;
+}
+
 int game_eval_fitness_prec(game_t h, const float* pop, int32_t P, int32_t precision,
                            double* fit_out) {
   g_last_error.clear();

@@ -37,6 +37,10 @@ GAME_SEL_RANKING = 1
 GAME_SEL_ROULETTE = 2
 GAME_HOOK_FAIL_ALLOC = 1
 GAME_HOOK_STALL_NS = 2
+GAME_KERNEL_FP32 = 1
+GAME_KERNEL_TC = 2
+GAME_KERNEL_TC_PAIR = 3
+GAME_KERNEL_GRAM = 4
 
 _ERR_NAMES = {GAME_EINVAL: "GAME_EINVAL", GAME_ENOMEM: "GAME_ENOMEM", GAME_ECUDA: "GAME_ECUDA",
               GAME_ETIMEOUT: "GAME_ETIMEOUT", GAME_ESTATE: "GAME_ESTATE"}
@@ -52,7 +56,7 @@ EXPORTED = ("game_params_default", "game_create", "game_get_shape", "game_eval_f
             "game_surrogate_train", "game_surrogate_params", "game_surrogate_set_params",
             "game_surrogate_last", "game_gram", "game_predict", "game_classify",
             "game_save", "game_load", "game_test_hook", "game_eval_sse", "game_breed",
-            "game_set_fitness")
+            "game_set_fitness", "game_plan_info")
 
 
 class GameError(RuntimeError):
@@ -187,6 +191,7 @@ def load(build_if_missing: bool = True):
         "game_eval_sse": [vp, vp, i32, dp],
         "game_breed": [vp, u64],
         "game_set_fitness": [vp, dp],
+        "game_plan_info": [vp, i32, i32, vp],
         "game_classify": [vp, vp, vp, vp, i64, ctypes.c_double, ctypes.POINTER(game_confusion)],
     }
     for name, args in sig.items():
@@ -391,6 +396,7 @@ class Game:
         self._keep = (X, y)
         self.h = game_create(X, y, degree, basis, prm, stream)
         self.M, self.N, self.K, self.P = game_get_shape(self.h)
+        self.precision = prm.precision
 
     def eval_fitness(self, pop, precision=None):
         if isinstance(pop, np.ndarray):
@@ -518,6 +524,18 @@ class Game:
             raise ValueError("out holds fewer than P values")
         _check(load().game_eval_sse(self.h, _ptr(pop), P, _ptr(out)))
         return out
+
+    def plan(self, precision=None, P=None):
+        """The launch plan of an evaluation (game_plan_info) as a dict."""
+        info = np.zeros(8, dtype=np.int32)
+        prec = self.precision if precision is None else precision
+        _check(load().game_plan_info(self.h, prec, self.P if P is None else P, _ptr(info)))
+        names = {GAME_KERNEL_FP32: "fitness_fp32_kernel", GAME_KERNEL_TC: "fitness_tc_kernel",
+                 GAME_KERNEL_TC_PAIR: "fitness_tc2_kernel", GAME_KERNEL_GRAM: "quad_kernel"}
+        keys = ("kernel", "tile", "kblocks", "stages", "slots", "staged", "ctas", "smem")
+        d = dict(zip(keys, (int(v) for v in info)))
+        d["kernel"] = names[d["kernel"]]
+        return d
 
     def breed(self, seed):
         """The operators of one generation, without evaluating the result."""

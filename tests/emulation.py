@@ -136,10 +136,11 @@ def bf16_operands(X, pop, d, basis):
     return a0, bf16(A).astype(np.float64), bf16(phi).astype(np.float64), amb
 
 
-def model(form, X, y, pop, d, basis):
+def model(form, X, y, pop, d, basis, error="mse"):
     """Fitness of every chromosome under the form's operand roundings, with
     exact products and sums, and the per-chromosome tolerance of a kernel
-    around it (see `tolerance`). Returns (fit [P], tol [P])."""
+    around it (see `tolerance`). error: "mse", "rmse" or "mae" (mean
+    absolute residual). Returns (fit [P], tol [P])."""
     y = np.asarray(y, dtype=np.float32)
     a0, A = _gene_rows(pop)
     phi, delta = expansion_fp32(X, d, basis)
@@ -199,8 +200,17 @@ def model(form, X, y, pop, d, basis):
         raise ValueError(form)
     ya = (y[:, None].astype(np.float32) - a0[None, :].astype(np.float32)).astype(np.float32)
     r = ya.astype(np.float64) - u[None, :] * D
+    dOut = u[None, :] * dD
+    if error == "mae":
+        # |mean |r'| - mean |r|| <= mean |dOut|, plus the epilogue's FP32 sums
+        fit = np.mean(np.abs(r), axis=0)
+        yv = np.asarray(y, dtype=np.float64)
+        return fit, np.mean(dOut, axis=0) + 1e-5 * fit + 1e-7 * np.sqrt(np.mean(yv * yv))
     fit = np.mean(r * r, axis=0)
-    tol = tolerance(fit, u[None, :] * dD, y)
+    tol = tolerance(fit, dOut, y)
+    if error == "rmse":
+        # |sqrt(a) - sqrt(b)| <= |a - b| / sqrt(b)
+        return np.sqrt(fit), tol / np.sqrt(fit)
     return fit, tol
 
 

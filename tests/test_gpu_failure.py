@@ -31,16 +31,21 @@ def disarm():
     game.game_test_hook(game.GAME_HOOK_STALL_NS, 0)
 
 
-# staged features (degree 4), features read from L2 (Chebyshev degree 8),
-# FP8 and the split form
-@pytest.mark.parametrize("degree,form", [(4, "bf16"), (8, "bf16"), (4, "fp8"), (4, "bf16x3")])
-def test_expired_wait_reports_timeout_and_the_handle_recovers(degree, form):
+# one-SM kernel: staged features (degree 4), features read from L2
+# (Chebyshev degree 8), FP8 and the split form; paired-SM kernel: 48 features
+# of degree 6 (the one-SM plan would narrow its tile)
+@pytest.mark.parametrize("N,degree,form,kernel", [
+    (8, 4, "bf16", "fitness_tc_kernel"), (8, 8, "bf16", "fitness_tc_kernel"),
+    (8, 4, "fp8", "fitness_tc_kernel"), (8, 4, "bf16x3", "fitness_tc_kernel"),
+    (48, 6, "bf16", "fitness_tc2_kernel")])
+def test_expired_wait_reports_timeout_and_the_handle_recovers(N, degree, form, kernel):
     prec = {"bf16": game.GAME_PREC_BF16, "fp8": game.GAME_PREC_FP8,
             "bf16x3": game.GAME_PREC_BF16X3}[form]
-    pr = dg.regression(17, 20000, 8, 3, 0.05, degree=degree)
+    pr = dg.regression(17, 20000, N, 3, 0.05, degree=degree)
     pop = dg.random_population(5, 300, pr.K)
     want, tol = model(form, pr.X, pr.y, pop, degree, CHEB)
     with game.Game(pr.X, pr.y, degree, CHEB, P=64, precision=prec, rescore_top=0) as g:
+        assert g.plan(P=300)["kernel"] == kernel
         game.game_test_hook(game.GAME_HOOK_STALL_NS, 20_000_000)    # 20 ms
         with pytest.raises(game.GameError) as ei:
             g.eval_fitness(pop)

@@ -11,7 +11,9 @@
 // recurrence from column to column, so a run inside one feature costs one FMA
 // per value. Columns >= Kp are zero (padding of the contraction length).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "../../include/game.h"
 
@@ -233,6 +235,78 @@ __device__ __forceinline__ void cheb_cross1(uint32_t desc, int d, int N, const f
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       if (e >= nvalid) v[e] = 0.f;
+  }
+}
+
+// ---- whole-feature groups (the batched generator) ----
+// With W = B d columns per feature, a group is the shortest run of whole
+// features that fills whole 8-column chunks: F = 8 / gcd(W, 8) features, G =
+// F W columns, G / 8 chunks, and group g starts at column g G. With the basis
+// and the degree known at compile time, a group's values are straight-line
+// code: one FMA per value after each feature's start (T_1 = x, or one
+// sincosf), the F features' recurrences independent of one another, no
+// branch and no restart. The values are those of gen_chunk bit for bit (the
+// same operations from the same start values).
+constexpr int const_gcd(int a, int b) { return b == 0 ? a : const_gcd(b, a % b); }
+
+template <int BASIS, int D>
+struct FeatureGroup {
+  static constexpr int W = (BASIS == GAME_BASIS_TRIG ? 2 : 1) * D;
+  static constexpr int F = 8 / const_gcd(W, 8);
+  static constexpr int G = F * W;
+  static constexpr int CH = G / 8;
+  // groups generated together before their chunks are stored (several
+  // groups at once, for more independent recurrences, measured slower)
+  static constexpr int U = 1;
+};
+
+// The values of NF consecutive whole features x[0..NF) (NF a multiple of the
+// group's F), rounded to BF16 and packed in column pairs: pk[k] holds columns
+// 2k and 2k + 1, the lower column in the low half. Features f >= nf (past the
+// problem's last feature) give zeros. The NF recurrences are independent, so
+// the compiler can interleave them.
+template <int BASIS, int D, int NF>
+__device__ __forceinline__ void features_bf16(const float (&x)[NF], int nf,
+                                              uint32_t (&pk)[NF * (BASIS == GAME_BASIS_TRIG ? 2 : 1) * D / 2]) {
+  constexpr int W = (BASIS == GAME_BASIS_TRIG ? 2 : 1) * D;
+  float lo = 0.f;   // the pending even column
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const bool on = f < nf;
+    float fm, fv, c2;
+    float s1 = 0.f;
+    if (BASIS == GAME_BASIS_CHEB) {
+      c2 = x[f] + x[f];
+      fm = 1.f;
+      fv = x[f];
+    } else {
+      float c1;
+      sincosf(x[f], &s1, &c1);
+      c2 = c1 + c1;
+      fm = 1.f;   // cos(0 x)
+      fv = c1;    // cos(1 x)
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      if (e > 0) {
+        if (BASIS == GAME_BASIS_TRIG && e == D) {
+          fm = 0.f;   // sin(0 x)
+          fv = s1;    // sin(1 x)
+        } else {
+          const float fn = fmaf(c2, fv, -fm);
+          fm = fv;
+          fv = fn;
+        }
+      }
+      const int c = f * W + e;
+      const float val = on ? fv : 0.f;
+      if (c & 1) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, val);
+        pk[c >> 1] = *reinterpret_cast<const uint32_t*>(&b2);
+      } else {
+        lo = val;
+      }
+    }
   }
 }
 

@@ -33,8 +33,7 @@ namespace game {
 
 namespace {
 
-constexpr int kPhiBudget = 128 * 1024;   // expansion K-blocks of one item
-constexpr int kXBudget = 32 * 1024;      // features of one item
+constexpr int kPhiBudget = 156 * 1024;   // expansion K-blocks of one item
 constexpr int kMaxSmemBatch = 232448;
 constexpr int kMaxKBBatch = 32;          // per-K-block phases live in 32-bit masks
 
@@ -176,9 +175,8 @@ struct game_batch {
   BatchRun* runs_d = nullptr;
   BatchGaRun* ga_d = nullptr;
   // fitness launch of the current tile choice
-  int2* items = nullptr;
-  int* sched = nullptr;
-  int* cta_begin = nullptr;
+  BatchItem* recs = nullptr;
+  int* work = nullptr;        // the fitness launch's item counter
   double* part = nullptr;
   size_t items_cap = 0, part_cap = 0;
   BatchArgs args{};
@@ -228,7 +226,8 @@ bool is_dev(const void* p) {
 
 // Shared-memory bytes of one item of run r at tile width bn.
 bool tile_fits(const Shape& s, int KB, int bn) {
-  return KB * bn * 128 <= kPhiBudget && s.N * bn * 4 <= kXBudget;
+  (void)s;
+  return KB * bn * 128 <= kPhiBudget;
 }
 
 int heuristic_bn(const Shape& s, int KB) {
@@ -270,59 +269,49 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
   int64_t part_total = 0;
   std::vector<int2> items;
   std::vector<double> cost;
-  int KBmax = 1, bn_max = 32, phi_bytes = 0, x_bytes = 0;
+  int KBmax = 1, set_max = 32, phi_bytes = 0;
   for (int r : which) {
     BatchRun& R = runs[r];
     R.part_base = part_total;
     part_total += (int64_t)R.ntiles * R.Ppad;
     KBmax = std::max(KBmax, R.KB);
-    bn_max = std::max(bn_max, R.BN);
+    set_max = std::max(set_max, std::min(R.C, 256 / R.BN) * R.BN);
     phi_bytes = std::max(phi_bytes, R.KB * R.BN * 128);
-    x_bytes = std::max(x_bytes, R.N * R.BN * 4);
-    // per item: MMAs ~ C KB BN, expansion ~ KB BN, epilogue ~ C BN, plus a fixed cost
-    const double c = (double)R.BN * (R.C * R.KB + 0.5 * R.KB + 0.5 * R.C) + 2000.0;
+    // cycles per item, roughly: the expansion (64 BN values per K-block at
+    // about 4 per cycle, sincosf once per feature for the trigonometric
+    // basis), the MMAs (about 2.5 BN per K-block and chromosome tile), the
+    // epilogue (about BN per chromosome tile) and a fixed cost
+    const double trig = R.basis == GAME_BASIS_TRIG ? 1.0 + 2.0 / R.d : 1.0;
+    const double c = (double)R.BN * R.KB * (16.0 * trig + 2.5 * R.C) + (double)R.BN * R.C +
+                     3000.0;
     for (int t = 0; t < R.ntiles; ++t) {
       items.push_back(make_int2(r, t));
       cost.push_back(c);
     }
   }
   if (KBmax > kMaxKBBatch) return bfail(GAME_EINVAL, "contraction too long for the batch");
-  const int smem = batch_smem_bytes(phi_bytes, x_bytes, KBmax);
+  const int smem = batch_smem_bytes(phi_bytes, KBmax);
   if (smem > kMaxSmemBatch) return bfail(GAME_EINVAL, "batch tiles exceed shared memory");
   BCK(prepare_fitness_batch(smem));   // outside any stream capture
   const int64_t n = (int64_t)items.size();
   const int grid = (int)std::min<int64_t>(b->num_sms, std::max<int64_t>(n, 1));
-  // greedy longest-first
-  std::vector<int> order(n);
-  for (int64_t i = 0; i < n; ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  typedef std::pair<double, int> Load;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int c = 0; c < grid; ++c) heap.push(Load(0.0, c));
-  std::vector<std::vector<int>> lists(grid);
-  for (int i : order) {
-    Load l = heap.top();
-    heap.pop();
-    lists[l.second].push_back(i);
-    heap.push(Load(l.first + cost[i], l.second));
-  }
-  std::vector<int> sched;
-  std::vector<int> begin(grid + 1, 0);
-  for (int c = 0; c < grid; ++c) {
-    std::sort(lists[c].begin(), lists[c].end());   // items are run-major: by run, then tile
-    begin[c] = (int)sched.size();
-    sched.insert(sched.end(), lists[c].begin(), lists[c].end());
-  }
-  begin[grid] = (int)sched.size();
+  // Dynamic schedule: every CTA takes the next item of one list from a
+  // global counter, so an SM that runs slower (its loads travel further, for
+  // one) simply takes fewer items. The list runs by tile width, widest first
+  // (a change of width drains the expansion buffers, so each CTA changes
+  // width at most three times), and within a width longest first.
+  std::vector<int> sched(n);
+  for (int64_t i = 0; i < n; ++i) sched[i] = (int)i;
+  std::stable_sort(sched.begin(), sched.end(), [&](int x, int y) {
+    const int bx = runs[items[x].x].BN, by = runs[items[y].x].BN;
+    return bx != by ? bx > by : cost[x] > cost[y];
+  });
   // device buffers (grown on demand)
   if ((size_t)std::max<int64_t>(n, 1) > b->items_cap) {
-    dfree(b->items);
-    dfree(b->sched);
-    b->items = nullptr;
-    b->sched = nullptr;
+    dfree(b->recs);
+    b->recs = nullptr;
     b->items_cap = 0;
-    if (dalloc(&b->items, (size_t)std::max<int64_t>(n, 1)) != cudaSuccess ||
-        dalloc(&b->sched, (size_t)std::max<int64_t>(n, 1)) != cudaSuccess) {
+    if (dalloc(&b->recs, (size_t)std::max<int64_t>(n, 1)) != cudaSuccess) {
       cudaGetLastError();
       return bfail(GAME_ENOMEM, "batch item lists");
     }
@@ -338,29 +327,47 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
     }
     b->part_cap = (size_t)std::max<int64_t>(part_total, 1);
   }
+  // the items in CTA order, with everything each role of the kernel reads
+  std::vector<BatchItem> recs(sched.size());
+  for (size_t k = 0; k < sched.size(); ++k) {
+    const int2 it = items[sched[k]];
+    const BatchRun& R = runs[it.x];
+    BatchItem& I = recs[k];
+    I = BatchItem{};
+    I.Xt = R.Xt;
+    I.y = R.y;
+    I.popA = R.popA;
+    I.a0 = R.a0;
+    I.prow = b->part + R.part_base + (int64_t)it.y * R.Ppad;
+    I.m0 = (int64_t)it.y * R.BN;
+    I.N = R.N;
+    I.d = R.d;
+    I.basis = R.basis;
+    I.Kp = R.Kp;
+    I.KB = R.KB;
+    I.C = R.C;
+    I.BN = R.BN;
+    I.nmma_last = R.nmma_last;
+    I.valid = (int)std::min<int64_t>(R.BN, R.M - I.m0);
+    I.CG = std::min(R.C, 256 / R.BN);
+  }
   BCK(cudaMemcpyAsync(b->runs_d, runs.data(), sizeof(BatchRun) * b->R, cudaMemcpyHostToDevice,
                       b->st));
-  if (n > 0) {
-    BCK(cudaMemcpyAsync(b->items, items.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, b->st));
-    BCK(cudaMemcpyAsync(b->sched, sched.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->st));
-  }
-  BCK(cudaMemcpyAsync(b->cta_begin, begin.data(), sizeof(int) * (grid + 1),
-                      cudaMemcpyHostToDevice, b->st));
+  if (n > 0)
+    BCK(cudaMemcpyAsync(b->recs, recs.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice,
+                        b->st));
   BCK(cudaStreamSynchronize(b->st));   // host vectors go out of scope
   BatchArgs& a = b->args;
-  a.runs = b->runs_d;
-  a.items = b->items;
-  a.sched = b->sched;
-  a.cta_begin = b->cta_begin;
-  a.part = b->part;
+  a.recs = b->recs;
+  a.nitems = (int)n;
+  a.work = b->work;
   a.status = b->status;
   a.KBmax = KBmax;
-  a.bn_max = bn_max;
   a.phi_bytes = phi_bytes;
-  a.x_bytes = x_bytes;
   int cols = 32;
-  while (cols < 2 * bn_max) cols <<= 1;
-  a.tmem_cols = cols;
+  while (cols < set_max) cols <<= 1;
+  a.set_cols = cols;
+  a.tmem_cols = 2 * cols;
   b->grid = grid;
   b->smem = smem;
   b->nitems = n;
@@ -369,6 +376,7 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
 
 int launch_fitness(game_batch* b) {
   if (b->nitems == 0) return GAME_OK;
+  BCK(cudaMemsetAsync(b->work, 0, sizeof(int), b->st));   // the item counter
   BCK(launch_fitness_batch(b->args, b->grid, b->smem, b->st));
   return GAME_OK;
 }
@@ -528,9 +536,8 @@ void destroy_batch(game_batch* b) {
   dfree(b->chrom_begin);
   dfree(b->runs_d);
   dfree(b->ga_d);
-  dfree(b->items);
-  dfree(b->sched);
-  dfree(b->cta_begin);
+  dfree(b->recs);
+  dfree(b->work);
   dfree(b->part);
   if (b->own_stream) cudaStreamDestroy(b->st);
   delete b;
@@ -632,7 +639,7 @@ int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* p
       dalloc(&b->popA, nA) != cudaSuccess || dalloc(&b->a0, na0) != cudaSuccess ||
       dalloc(&b->gens, R) != cudaSuccess || dalloc(&b->status, 4) != cudaSuccess ||
       dalloc(&b->chrom_begin, R) != cudaSuccess || dalloc(&b->runs_d, R) != cudaSuccess ||
-      dalloc(&b->ga_d, R) != cudaSuccess || dalloc(&b->cta_begin, b->num_sms + 1) != cudaSuccess) {
+      dalloc(&b->ga_d, R) != cudaSuccess || dalloc(&b->work, 1) != cudaSuccess) {
     cudaGetLastError();
     return bail(bfail(GAME_ENOMEM, "batch device memory"));
   }

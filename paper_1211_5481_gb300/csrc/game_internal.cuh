@@ -126,16 +126,27 @@ struct BatchRun {           // one problem, as the batched kernels see it
   int64_t part_base;        // first partial row of this problem (doubles)
   int N, d, basis, Kp, K, P, Ppad, C, KB, BN, nmma_last, ntiles;
 };
-struct BatchArgs {
-  const BatchRun* runs;
-  const int2* items;        // (problem, pattern tile), problem-major
-  const int* sched;         // item indices, grouped by CTA
-  const int* cta_begin;     // [grid + 1] ranges of sched per CTA
-  double* part;             // partial rows: part_base_r + t Ppad_r
-  int* status;
-  int KBmax, bn_max, phi_bytes, x_bytes, tmem_cols;
+// One work item (problem r, pattern tile t) as every role of the batched
+// fitness kernel reads it: one 96-byte load per item, no indirection.
+struct alignas(16) BatchItem {
+  const float* Xt;          // the problem's features [Mpad/128][N][128]
+  const float* y;           // the problem's targets [Mpad]
+  const uint8_t* popA;      // the problem's BF16 operand image
+  const float* a0;          // the problem's bias genes [Ppad]
+  double* prow;             // this tile's partial row: part + part_base_r + t Ppad_r
+  int64_t m0;               // first pattern of the tile
+  int N, d, basis, Kp, KB, C, BN, nmma_last, valid;
+  int CG;                   // chromosome tiles per accumulator set: min(C, 256 / BN)
+  int pad0, pad1;
 };
-int batch_smem_bytes(int phi_bytes, int x_bytes, int KBmax);
+struct BatchArgs {
+  const BatchItem* recs;    // the items in the order CTAs take them
+  int nitems;
+  int* work;                // next item to take (zeroed before each launch)
+  int* status;
+  int KBmax, set_cols, phi_bytes, tmem_cols;   // accumulator set s at tmem + s set_cols
+};
+int batch_smem_bytes(int phi_bytes, int KBmax);
 // sets the kernel's dynamic shared-memory limit (call outside stream capture)
 cudaError_t prepare_fitness_batch(int smem_bytes);
 // launch only (capturable)

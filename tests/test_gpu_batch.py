@@ -148,3 +148,42 @@ def test_batched_workload_sample(orc):
                                           bits(orc.generation(pop, fit, 1000 + r, gen, prm)))
             ref = orc.fitness(pr.X, pr.y, npop, pr.degree, pr.basis)
             assert np.all(np.abs(nfit - ref) <= bf16_bound(ref, pr.X, npop, pr.degree, pr.basis))
+
+
+# every degree the batched generator specialises (1..10) and two it does not
+# (11, 12: the generic chunk generator), for both bases; feature counts chosen
+# so that feature groups, 8-column chunks and 64-column K-blocks meet at
+# different offsets; trigonometric features over [-3, 3]
+DEGREE_RUNS = [(200 + 97 * d + 31 * b, [3, 7, 13, 5, 9, 11, 4, 6, 10, 12, 2, 8][d - 1] + b,
+                d, basis, 20 + 13 * d, 100 + 16 * d + b)
+               for b, basis in enumerate((CHEB, TRIG)) for d in range(1, 13)]
+
+
+@pytest.mark.parametrize("tiles", [None, 32, 64, 128])
+def test_batch_every_degree_matches_cpu_model(tiles):
+    """Each run's fitness against the CPU model of the BF16 form (operands
+    rounded as the kernel rounds them, exact products): only the FP32
+    accumulation order and ambiguous roundings may differ. Tile widths of
+    32, 64 and 128 patterns put 8, 4 and 2 expansion threads on each pattern
+    row (each a contiguous range of whole features)."""
+    from emulation import model
+    args, probs = [], []
+    for (M, N, d, basis, P, seed) in DEGREE_RUNS:
+        pr = dg.regression(seed, M, N, min(d, 4), 0.05, degree=d, basis=basis)
+        X = (pr.X * np.float32(3.0 if basis == TRIG else 1.0)).astype(np.float32)
+        args.append((X, pr.y, d, basis, P, seed))
+        probs.append((X, pr.y, d, basis))
+    kw = {"autotune": False}
+    if tiles is not None:
+        kw["tiles"] = [tiles] * len(args)
+    with game.Batch(args, **kw) as b:
+        if tiles is not None:
+            assert b.tiles().tolist() == [tiles] * len(args)
+        for gen in range(2):
+            if gen:
+                b.generation()
+            for r, (X, y, d, basis) in enumerate(probs):
+                pop, fit, _ = b.run(r)
+                want, tol = model("bf16", X, y, pop, d, basis)
+                err = np.abs(fit - want)
+                assert np.all(err <= tol), (r, DEGREE_RUNS[r], float((err / tol).max()))

@@ -574,6 +574,8 @@ int check_status(game_ctx* h) {
   if (st != kDevOk) {
     CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
     CK(cudaStreamSynchronize(h->st));
+    if (st == kDevSmemBase)
+      return fail(GAME_ECUDA, "dynamic shared memory less aligned than planned; results are void");
     return fail(GAME_ETIMEOUT, "a kernel wait timed out; results of the affected calls are void");
   }
   return GAME_OK;
@@ -873,13 +875,16 @@ int game_create(const float* X, const float* y, int64_t M, int32_t N, int32_t de
   int bad_h[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
   if (e == cudaSuccess) e = launch_relayout_X(dX, dy, s, h->Xt, h->y, h->status, h->st);
+  // where dynamic shared memory starts, for the tensor-core launch plans
+  if (e == cudaSuccess) e = launch_smem_base_probe(h->status + 2, h->st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bad_h, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    e = cudaMemcpyAsync(bad_h, h->status, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 4 * sizeof(int), h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   dev_free(tmpX);
   dev_free(tmpy);
   if (e != cudaSuccess) return bail(cuda_fail(e, "training-set upload"));
+  note_smem_base_pad(bad_h[2]);
   if (bad_h[0]) return bail(fail(GAME_EINVAL, "X or y holds NaN or Inf"));
   if (bad_h[1]) return bail(fail(GAME_EINVAL, "Chebyshev basis needs features in [-1, 1]"));
 

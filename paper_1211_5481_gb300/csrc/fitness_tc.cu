@@ -60,6 +60,8 @@
 // copies and MMAs in flight, frees tensor memory and returns.
 #include <cuda_fp8.h>
 
+#include <atomic>
+
 #include "basis.cuh"
 #include "game_internal.cuh"
 #include "tc_common.cuh"
@@ -90,6 +92,9 @@ struct TcArgs {
                 // next tile's first K-blocks be written while this tile's MMAs run
   int xstage;   // 1: the tile's features are bulk-copied into shared memory;
                 // 0: read from global memory (L2) by the expansion warps
+  int ystage;   // 1 (with xstage 0): warp 2 bulk-copies each tile's targets into
+                // a two-slot shared buffer the epilogue reads
+  int slack;    // bytes reserved for aligning the dynamic shared memory to 1024
   const float* Xt;
   const float* y;
   const uint8_t* popA;
@@ -103,22 +108,24 @@ struct TcArgs {
 };
 
 struct SmemPlan {
-  int phi, ast, xs, cs, tab, bars, total;
+  int phi, ast, xs, ys, cs, tab, bars, total;
 };
 
-__host__ __device__ inline int num_bars(int NS, int stages) { return 2 * stages + 2 * NS + 7; }
+__host__ __device__ inline int num_bars(int NS, int stages) { return 2 * stages + 2 * NS + 11; }
 
-// Byte offsets of the shared-memory regions from the 1024-aligned base.
+// Byte offsets of the shared-memory regions from the 1024-aligned base;
+// total includes `slack` bytes for aligning the base.
 __host__ __device__ inline SmemPlan smem_plan(int KB, int NS, int BN, int N, int stages, int F,
-                                              int xstage) {
+                                              int xstage, int ystage, int slack) {
   SmemPlan s;
   s.phi = 0;
   s.ast = s.phi + NS * form_nphi(F) * BN * 128;
   s.xs = s.ast + stages * form_na(F) * (int)kABytes;
-  s.cs = s.xs + (xstage ? N * BN * 4 : 0);
+  s.ys = s.xs + (xstage ? N * BN * 4 : 0);
+  s.cs = s.ys + (ystage ? 2 * BN * 4 : 0);
   s.tab = s.cs + (F == kFormFP8 ? KB * 128 * 4 : 0);
   s.bars = (s.tab + KB * (form_cols(F) / 8) * 4 + 7) & ~7;
-  s.total = s.bars + num_bars(NS, stages) * 8 + 16 + 1024;   // + alignment slack
+  s.total = s.bars + num_bars(NS, stages) * 8 + 16 + slack;
   return s;
 }
 
@@ -132,10 +139,19 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int BN = a.BN, KB = a.KB, N = a.N, S = a.stages, NS = a.NS;
-  const SmemPlan sp = smem_plan(KB, NS, BN, N, S, F, a.xstage);
+  // the plan reserves a.slack bytes for aligning the base: a base that needs
+  // more (the host plans from a probe of where dynamic shared memory starts)
+  // ends the launch before any shared memory is touched
+  const uint32_t pad = (1024u - (ptx::smem_addr(smem_raw) & 1023u)) & 1023u;
+  if (pad > (uint32_t)a.slack) {
+    if (threadIdx.x == 0) atomicExch(a.status, (int)kDevSmemBase);
+    return;
+  }
+  const SmemPlan sp = smem_plan(KB, NS, BN, N, S, F, a.xstage, a.ystage, a.slack);
   uint8_t* phi = base + sp.phi;
   uint8_t* ast = base + sp.ast;
   float* xs = reinterpret_cast<float*>(base + sp.xs);
+  float* ys = reinterpret_cast<float*>(base + sp.ys);
   float* cs = reinterpret_cast<float*>(base + sp.cs);
   uint32_t* tab = reinterpret_cast<uint32_t*>(base + sp.tab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + sp.bars);
@@ -148,7 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
   uint64_t* x_full = acc_empty + 2;
   uint64_t* x_empty = x_full + 1;
   uint64_t* drain = x_empty + 1;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* y_full = drain + 1;   // [2]
+  uint64_t* y_empty = y_full + 2;  // [2]
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(y_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -168,6 +186,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
     ptx::mbar_init(ptx::smem_addr(x_full), 1);
     ptx::mbar_init(ptx::smem_addr(x_empty), kBasisThreads);
     ptx::mbar_init(ptx::smem_addr(drain), 1);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_addr(&y_full[b]), 1);
+      ptx::mbar_init(ptx::smem_addr(&y_empty[b]), kEpiThreads);
+    }
     *abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::fence_proxy_async_smem();
@@ -371,6 +393,27 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       }
       if (issued > 0) wait_bar_drain(ptx::smem_addr(x_full), (issued - 1) & 1, a.status);
     }
+    // ---------------- Y producer (features read from L2) ----------------
+    // each tile's targets into slot it & 1, released by the 256 epilogue
+    // threads after the tile's last chromosome tile
+    if (lane == 0 && a.ystage) {
+      int issued = 0;
+      for (int it = 0; it < my_tiles; ++it) {
+        const int b = it & 1;
+        if (!wait_bar(ptx::smem_addr(&y_empty[b]), ((it >> 1) & 1) ^ 1, abort_flag, a.status))
+          break;
+        const int64_t m0 = ((int64_t)blockIdx.x + (int64_t)it * G) * BN;
+        ptx::mbar_arrive_expect_tx(ptx::smem_addr(&y_full[b]), (uint32_t)BN * 4);
+        ptx::bulk_g2s(ptx::smem_addr(ys + b * BN), a.y + m0, (uint32_t)BN * 4,
+                      ptx::smem_addr(&y_full[b]));
+        ++issued;
+      }
+      // own copies in flight: the last phase armed on each slot
+      for (int b = 0; b < 2 && b < issued; ++b) {
+        const int uses = (issued - b + 1) / 2;
+        wait_bar_drain(ptx::smem_addr(&y_full[b]), (uint32_t)(uses - 1) & 1u, a.status);
+      }
+    }
   } else if (warp >= kEpiWarp0 && warp < kBasisWarp0) {
     // ---------------- epilogue ----------------
     const int qw = warp & 3;
@@ -387,7 +430,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
       const int64_t m0 = ((int64_t)blockIdx.x + (int64_t)it * G) * BN;
       const int64_t rem = a.M - m0 - col_lo;
       const int valid = (half >= NH || rem <= 0) ? 0 : (rem >= HW ? HW : (int)rem);
-      const float* yt = a.y + m0 + col_lo;
+      const bool ysm = a.ystage != 0;
+      if (ysm) {
+        ok = wait_bar(ptx::smem_addr(&y_full[it & 1]), (it >> 1) & 1, abort_flag, a.status);
+        if (!ok) break;
+      }
+      const float* yt = ysm ? ys + (it & 1) * BN + col_lo : a.y + m0 + col_lo;
       for (int c = 0; c < a.C; ++c) {
         const uint32_t buf = acc_it & 1, u = acc_it >> 1;
         ok = wait_bar(ptx::smem_addr(&acc_full[buf]), u & 1, abort_flag, a.status);
@@ -411,12 +459,14 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           for (int k = 0; k < nfull; k += 2) {
             const bool has_b = k + 1 < nfull;
             if (has_b) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 1) * 32, vb);
-            epi_chunk<F == kFormFP8, ABS>(va, yt + k * 32, bias2, negu2, s2);
+            if (ysm) epi_chunk<F == kFormFP8, ABS, true>(va, yt + k * 32, bias2, negu2, s2);
+            else epi_chunk<F == kFormFP8, ABS>(va, yt + k * 32, bias2, negu2, s2);
             if (has_b) {
               ptx::tmem_ld32_wait(vb);
               const bool has_a = k + 2 < nfull;
               if (has_a) ptx::tmem_ld32_issue(tbase + (uint32_t)(k + 2) * 32, va);
-              epi_chunk<F == kFormFP8, ABS>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
+              if (ysm) epi_chunk<F == kFormFP8, ABS, true>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
+              else epi_chunk<F == kFormFP8, ABS>(vb, yt + (k + 1) * 32, bias2, negu2, s2);
               if (has_a) ptx::tmem_ld32_wait(va);
             }
           }
@@ -440,6 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         part_row[chrom] = (it == 0) ? tile_sse : part_row[chrom] + tile_sse;
         ++acc_it;
       }
+      if (ysm && ok) ptx::mbar_arrive(ptx::smem_addr(&y_empty[it & 1]));
     }
   } else if (warp >= kBasisWarp0) {
     // ---------------- expansion (basis) ----------------
@@ -761,6 +812,28 @@ TcPlan plan_tc_single(const Shape& s, int P, int num_sms, int form);
 // one-SM tiles): one-SM 0.50 ms, pairs 0.54 ms per evaluation; on the
 // surrogate workload (K' = 288, N = 48: one-SM 192-pattern tiles): one-SM
 // 6.57 ms, pairs 5.33 ms.
+namespace {
+int g_base_pad = 1024;
+__global__ void smem_base_probe_kernel(int* out) {
+  extern __shared__ uint8_t probe_smem[];
+  if (threadIdx.x == 0) *out = (int)((1024u - (ptx::smem_addr(probe_smem) & 1023u)) & 1023u);
+}
+}  // namespace
+
+void set_smem_base_pad(int pad) { g_base_pad = pad < 0 ? 1024 : (pad > 1024 ? 1024 : pad); }
+int smem_base_pad() { return g_base_pad; }
+void note_smem_base_pad(int pad) {
+  static std::atomic<int> seen{-1};   // largest padding probed so far
+  int cur = seen.load();
+  while (pad > cur && !seen.compare_exchange_weak(cur, pad)) {
+  }
+  set_smem_base_pad(seen.load());
+}
+cudaError_t launch_smem_base_probe(int* out, cudaStream_t st) {
+  smem_base_probe_kernel<<<1, 32, 16, st>>>(out);
+  return cudaGetLastError();
+}
+
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form) {
   const TcPlan one = plan_tc_single(s, P, num_sms, form);
   if (form == kFormBF16 && P > 128 && !(one.ok && one.BN == 256)) {
@@ -783,11 +856,14 @@ TcPlan plan_tc_single(const Shape& s, int P, int num_sms, int form) {
   // read from L2 instead of staged, which frees room for spare expansion
   // slots (the next tile's first K-blocks are written during this tile)
   const bool runs = form == kFormBF16 && s.basis == GAME_BASIS_CHEB && s.d % 8 == 0;
-  auto take = [&](int BN, int NS, int stages, int xstage, int sm) {
+  const int slack = smem_base_pad();
+  pl.slack = slack;
+  auto take = [&](int BN, int NS, int stages, int xstage, int ystage, int sm) {
     pl.BN = BN;
     pl.NS = NS;
     pl.stages = stages;
     pl.xstage = xstage;
+    pl.ystage = ystage;
     // at least half an SM's shared memory: one CTA per SM, so the tensor
     // memory allocation never waits on a co-resident CTA
     pl.smem_bytes = sm < kMinSmem ? kMinSmem : sm;
@@ -795,15 +871,19 @@ TcPlan plan_tc_single(const Shape& s, int P, int num_sms, int form) {
   };
   for (int i = 0; i < 5 && !pl.ok; ++i) {
     if (cands[i] == 192 && form != kFormBF16) continue;
+    // (features from L2, the targets also staged where they fit: the
+    // feature producer is idle then)
     if (runs && cands[i] % 128 == 0)
       for (int stages = 4; stages >= min_stages && !pl.ok; --stages)
-        for (int spare = pl.KB; spare >= 1 && !pl.ok; --spare) {
-          const int sm = smem_plan(pl.KB, pl.KB + spare, cands[i], s.N, stages, form, 0).total;
-          if (sm <= kMaxSmem) take(cands[i], pl.KB + spare, stages, 0, sm);
-        }
+        for (int spare = pl.KB; spare >= 1 && !pl.ok; --spare)
+          for (int ystage = 1; ystage >= 0 && !pl.ok; --ystage) {
+            const int sm = smem_plan(pl.KB, pl.KB + spare, cands[i], s.N, stages, form, 0,
+                                     ystage, slack).total;
+            if (sm <= kMaxSmem) take(cands[i], pl.KB + spare, stages, 0, ystage, sm);
+          }
     for (int stages = 4; stages >= min_stages && !pl.ok; --stages) {
-      const int sm = smem_plan(pl.KB, pl.KB, cands[i], s.N, stages, form, 1).total;
-      if (sm <= kMaxSmem) take(cands[i], pl.KB, stages, 1, sm);
+      const int sm = smem_plan(pl.KB, pl.KB, cands[i], s.N, stages, form, 1, 0, slack).total;
+      if (sm <= kMaxSmem) take(cands[i], pl.KB, stages, 1, 0, sm);
     }
   }
   if (!pl.ok) return pl;
@@ -846,6 +926,8 @@ cudaError_t launch_fitness_tc(const TcPlan& pl, const Shape& s, const float* Xt,
   a.stages = pl.stages;
   a.NS = pl.NS;
   a.xstage = pl.xstage;
+  a.ystage = pl.ystage;
+  a.slack = pl.slack;
   const int cols = form_cols(pl.form);
   const int last_cols = s.Kp - cols * (pl.KB - 1);
   a.nmma_last = (last_cols + cols / 4 - 1) / (cols / 4);

@@ -40,7 +40,9 @@ constexpr int kMaxTournament = 64;
 constexpr int kMaxRescore = 16;  // elite candidates re-scored at most
 
 // Status word written by kernels (0 = fine).
-enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevBadShape = 2 };
+// kDevSmemBase: a kernel found its dynamic shared memory less aligned than its
+// launch plan assumed and returned before using it
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevBadShape = 2, kDevSmemBase = 3 };
 
 struct Shape {
   int64_t M, Mpad;
@@ -90,6 +92,7 @@ __host__ __device__ constexpr int form_cols(int f) { return f == kFormFP8 ? 128 
 // the features are staged in shared memory, 0 when read from L2
 struct TcPlan {
   int form, BN, KB, NS, xstage, C, stages, grid, smem_bytes, tmem_cols, rows;
+  int ystage, slack;   // targets staged in shared memory; bytes kept for base alignment
   int pair;   // 1: the paired-SM kernel (fitness_tc2.cu), C even, grid of 2-CTA clusters
   bool ok;
 };
@@ -97,6 +100,15 @@ struct TcPlan {
 // more than one chromosome tile takes the paired-SM kernel where its shared
 // memory fits; every other case the one-SM kernel. Ppad = C * 128.
 TcPlan plan_tc(const Shape& s, int P, int num_sms, int form);
+// Bytes the one-SM tensor-core kernel's dynamic shared memory needs to reach a
+// 1024-byte boundary: 1024 (every case) until set_smem_base_pad records what a
+// probe found on the GPU; the plans keep that much slack, and the kernel checks.
+void set_smem_base_pad(int pad);
+int smem_base_pad();
+// records a probe's result: the largest padding any probe has found so far
+void note_smem_base_pad(int pad);
+// writes the probe's padding (0..1023) to *out (device memory) on stream st
+cudaError_t launch_smem_base_probe(int* out, cudaStream_t st);
 TcPlan plan_tc_pair(const Shape& s, int P, int num_sms);
 cudaError_t launch_fitness_tc_pair(const TcPlan& pl, const Shape& s, const float* Xt,
                                    const float* y, const uint8_t* popA, const float* a0, int Ppad,

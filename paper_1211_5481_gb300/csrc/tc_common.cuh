@@ -51,12 +51,15 @@ static __device__ void wait_bar_drain(uint32_t bar, uint32_t parity, int* status
 // SCALED = false: u = 1 and the residual is one packed subtraction; true
 // (FP8): -u * acc + (y - bias) as one packed FMA (one rounding, as the
 // subtraction is for u = 1).
-template <bool SCALED, bool ABS = false>
+// YS: the targets yc are in shared memory (else global memory, read through
+// the read-only path).
+template <bool SCALED, bool ABS = false, bool YS = false>
 __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], const float* yc,
                                           uint64_t bias2, uint64_t negu2, uint64_t& s2) {
 #pragma unroll
   for (int e4 = 0; e4 < 8; ++e4) {
-    const float4 yv = __ldg(reinterpret_cast<const float4*>(yc) + e4);
+    const float4 yv = YS ? reinterpret_cast<const float4*>(yc)[e4]
+                         : __ldg(reinterpret_cast<const float4*>(yc) + e4);
     const uint64_t ya = ptx::f2_sub(ptx::f2_pack(yv.x, yv.y), bias2);
     const uint64_t yb = ptx::f2_sub(ptx::f2_pack(yv.z, yv.w), bias2);
     const uint64_t da = ptx::f2_pack(__uint_as_float(v[4 * e4 + 0]), __uint_as_float(v[4 * e4 + 1]));

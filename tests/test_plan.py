@@ -41,6 +41,10 @@ int main() {
   const long long Ms[] = {1, 777, 1000000};
   const int Ps[] = {1, 64, 129, 1024, 16384};
   long long plans = 0;
+  // 1024: the slack kept before any probe; 0: a probe found the dynamic
+  // shared memory already 1024-aligned (then the targets can be staged too)
+  for (int pad : {1024, 0}) {
+  set_smem_base_pad(pad);
   for (int form = 0; form < 3; ++form)
     for (int basis = 0; basis < 2; ++basis)
       for (int N : Ns)
@@ -72,6 +76,8 @@ int main() {
               CHECK(pl.KB == (s.Kp + form_cols(form) - 1) / form_cols(form), "KB %d", pl.KB);
               CHECK(pl.NS >= pl.KB && pl.NS <= 2 * pl.KB, "NS %d KB %d", pl.NS, pl.KB);
               CHECK(pl.xstage == 0 || pl.xstage == 1, "xstage");
+              CHECK(pl.ystage == 0 || (pl.ystage == 1 && pl.xstage == 0 && !pl.pair), "ystage");
+              CHECK(pl.pair || pl.slack == pad, "slack %d pad %d", pl.slack, pad);
               CHECK(pl.xstage == 1 || (form == kFormBF16 && basis == 0 && d % 8 == 0 &&
                                        pl.BN % 128 == 0), "unstaged features, form %d d %d BN %d",
                     form, d, pl.BN);
@@ -100,6 +106,17 @@ int main() {
             CHECK(fp.grid_y >= 1 && fp.grid_y <= (M + 127) / 128, "grid_y %d", fp.grid_y);
           }
         }
+  }
+  // the large classification shape stages its targets once the base is aligned
+  set_smem_base_pad(0);
+  TcPlan big = plan_tc(shape(1000000, 32, 8, 0), 1024, sms, kFormBF16);
+  CHECK(big.ok && big.BN == 256 && big.xstage == 0 && big.ystage == 1 && big.NS == 5 &&
+        big.stages == 4, "classification plan BN %d ystage %d NS %d stages %d", big.BN,
+        big.ystage, big.NS, big.stages);
+  set_smem_base_pad(1024);
+  big = plan_tc(shape(1000000, 32, 8, 0), 1024, sms, kFormBF16);
+  CHECK(big.ok && big.BN == 256 && big.ystage == 0 && big.NS == 5 && big.stages == 4,
+        "classification plan without alignment BN %d ystage %d", big.BN, big.ystage);
   printf("plans %lld violations %d\n", plans, bad);
   return bad != 0;
 }

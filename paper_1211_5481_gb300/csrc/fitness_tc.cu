@@ -669,6 +669,52 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
         *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
             make_uint4(wb[0], wb[1], wb[2], wb[3]);
     };
+    // Degree 8: chunk qd of K-block kb is feature kb 8 + qd's run of degrees
+    // 1..8 (zero past the last feature). Four chunks of both rows at a time:
+    // eight independent recurrences with no branch between them; the values
+    // are emit_run2x's, bit for bit.
+    auto emit_kblock_d8 = [&](uint8_t* phik, int kb, const float (&xa)[8], const float (&xb)[8]) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t wa[4][4], wb[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float xa0 = xa[h * 4 + u], xb0 = xb[h * 4 + u];
+          const float a2 = xa0 + xa0, b2 = xb0 + xb0;
+          float ta = xa0, tam = 1.f, tb = xb0, tbm = 1.f;
+          float va[8], vb[8];
+          va[0] = ta;
+          vb[0] = tb;
+#pragma unroll
+          for (int e = 1; e < 8; ++e) {
+            const float na = fmaf(a2, ta, -tam), nb = fmaf(b2, tb, -tbm);
+            tam = ta;
+            ta = na;
+            tbm = tb;
+            tb = nb;
+            va[e] = ta;
+            vb[e] = tb;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            wa[u][e] = bf16x2_bits(va[2 * e], va[2 * e + 1]);
+            wb[u][e] = bf16x2_bits(vb[2 * e], vb[2 * e + 1]);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qd = h * 4 + u;
+          const bool zero = kb * 8 + qd >= N;
+          *reinterpret_cast<uint4*>(phik + r0 * 128 + ((qd ^ (r0 & 7)) << 4)) =
+              zero ? make_uint4(0u, 0u, 0u, 0u)
+                   : make_uint4(wa[u][0], wa[u][1], wa[u][2], wa[u][3]);
+          if (R == 2)
+            *reinterpret_cast<uint4*>(phik + r1 * 128 + ((qd ^ (r1 & 7)) << 4)) =
+                zero ? make_uint4(0u, 0u, 0u, 0u)
+                     : make_uint4(wb[u][0], wb[u][1], wb[u][2], wb[u][3]);
+        }
+      }
+    };
     // both rows of a Chebyshev chunk that crosses feature runs (d >= 4)
     auto emit_cheb_cross2 = [&](uint8_t* phik, uint32_t desc, int qd) {
       float va[8], vb[8];
@@ -744,6 +790,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
           ok = slot_free(q);
           if (!ok) break;
           uint8_t* phik = phi + (size_t)(q % NS) * BN * 128;
+          if (a.d == 8) {
+            emit_kblock_d8(phik, kb, xa, xb);
+          } else {
 #pragma unroll
           for (int qd = 0; qd < 8; ++qd) {
             const uint32_t desc = tab[kb * 8 + qd];
@@ -756,6 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const TcArgs a)
             } else {
               emit_run2x(phik, desc, qd, xa[qd], xb[qd]);
             }
+          }
           }
           ptx::fence_proxy_async_smem();
           ptx::mbar_arrive(ptx::smem_addr(&phi_full[q % NS]));

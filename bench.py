@@ -86,7 +86,7 @@ def parse():
 # dram__bytes_write.sum of one ncu capture), per workload and form, with the
 # digest of the kernel sources the capture ran: reported only while the
 # sources are unchanged (null once the kernel has changed since).
-NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): (132.73e6 + 3.25e6, "decffcbcb7eceb9c")}
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): (132.64e6 + 3.02e6, "faf99fe9f6e36447")}
 KERNEL_SOURCES = ("fitness_tc.cu", "fitness_tc2.cu", "tc_common.cuh", "tc_ptx.cuh",
                   "basis.cuh")
 

@@ -43,6 +43,7 @@ CASES = [
     (1100, 128, 32, CHEB, 40, 1),    # K' = 4096: FP8 32 at its limit
     (3000, 6, 5, TRIG, 100, 8),      # features over [-8, 8]
     (1003, 5, 3, CHEB, 70, 1),       # K' = 15: a partial first MMA group
+    (2999, 9, 8, CHEB, 130, 1),      # degree 8 from L2 in BF16: zero chunks past feature 9
 ]
 
 

@@ -65,6 +65,9 @@ def parse():
                     help="surrogate workload: also run G generations of the FP64 oracle GA "
                          "(Gram form) and of the screened GPU GA and compare the best fitness")
     ap.add_argument("--no-fp32-leg", action="store_true")
+    ap.add_argument("--no-batched-leg", action="store_true",
+                    help="classification workload at one GPU: skip the batched workload's "
+                         "leg (256 independent runs, 10 generations) added to the line")
     ap.add_argument("--no-surrogate-leg", action="store_true",
                     help="classification workload at one GPU: skip the surrogate workload's "
                          "legs (4M patterns, screened BF16 vs plain FP32) added to the line")
@@ -324,11 +327,19 @@ def run_reference(args):
 
 
 def run_batched(args, torch, game, dev, world, rank):
+    """The batched workload's JSON line (see batched_line)."""
+    line = batched_line(args.steps, args.warmup, args.no_clocks, torch, game, dev, world)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def batched_line(steps, warmup, no_clocks, torch, game, dev, world):
     """256 independent GA runs (M log-uniform in [10^3, 2 10^5], N in 4..64,
     Chebyshev or trigonometric basis of degree 2..10, P log-uniform in
     [32, 512], regression targets), advanced together: one step = one
     generation of every run = one CUDA-graph replay (batched operators, pack,
-    one persistent tensor-core fitness launch, FP64 reduce)."""
+    one persistent tensor-core fitness launch, FP64 reduce). Returns the
+    workload's JSON line."""
     from paper_1211_5481_gb300 import datagen as dg
     runs = dg.batched_runs(R=256)
     args_b = [(pr.X, pr.y, pr.degree, pr.basis, pr.P, 1000 + r) for r, pr in enumerate(runs)]
@@ -340,15 +351,15 @@ def run_batched(args, torch, game, dev, world, rank):
     evals = float(sum(pr.M * pr.P for pr in runs))
     flops = float(sum(2.0 * pr.M * pr.P * (pr.K - 1) + 3.0 * pr.M * pr.P for pr in runs))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         b.generation()
     b.sync()
     if world > 1:
         torch.distributed.barrier()
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not args.no_clocks)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), enabled=not no_clocks)
     ev = []
     with torch.cuda.stream(bs):
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()   # L2 flush between steps, outside the timed events
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -372,7 +383,7 @@ def run_batched(args, torch, game, dev, world, rank):
     line = {
         "metric": METRIC, "value": whole_job_rate(evals, t_step, world), "unit": UNIT,
         "n_gpus": world,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_step * 1e3,
+        "steps": steps, "warmup": max(warmup, 3), "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
         "config": {"workload": "batched_256_runs", "runs": len(runs),
@@ -393,12 +404,11 @@ def run_batched(args, torch, game, dev, world, rank):
                          "frac": hbm_gbs / hbm_peak, "algorithmic_bytes": nbytes,
                          "note": "the same launch against the HBM roof (partials counted at "
                                  "128-pattern tiles)"},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 5 * steps,
         "clocks": clk,
     }
     b.close()
-    if rank == 0:
-        print(json.dumps(line))
+    return line
 
 
 def spearman(a, b):
@@ -865,6 +875,21 @@ def main():
                 "generations": of["generations"], "bf16_best": best_b,
                 "oracle_best": of["best"], "rel_diff": (best_b - of["best"]) / of["best"]}
         del X4, y4
+    bat = None
+    if world == 1 and not args.no_batched_leg:
+        # the batched workload (256 independent runs of uneven shape, one
+        # CUDA-graph replay per generation of all runs) beside the headline
+        bl = batched_line(10, 3, args.no_clocks, torch, game, dev, world)
+        bat = {"workload": bl["config"]["workload"], "runs": bl["config"]["runs"],
+               "sum_MP": bl["config"]["sum_MP"], "steps": bl["steps"],
+               "ms_per_generation": bl["ms_per_step"], "evals_per_s": bl["value"],
+               "generations_per_s": bl["generations_per_s"],
+               "fitness_kernel": bl["roofline"]["kernel"],
+               "fitness_kernel_ms": bl["roofline"]["kernel_ms"],
+               "roofline_frac": bl["roofline"]["frac"],
+               "roofline_peak": bl["roofline"]["peak"],
+               "tiles": bl["config"]["tiles"], "timing": bl["config"]["timing"],
+               "l2": bl["config"]["l2"], "clocks": bl["clocks"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_step, "higher_is_better": True,
@@ -890,6 +915,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "surrogate_workload": sur,
+        "batched_workload": bat,
         "gpu_launches": int(n_launch),
         "clocks": clk,
     }

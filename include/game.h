@@ -489,9 +489,18 @@ int game_sync(game_t h);
  *     handle's status word, drains its own copies and MMAs, frees its tensor
  *     memory, returns), so the call reports GAME_ETIMEOUT and the handle
  *     stays usable; 0 cancels a pending stall.
+ *   GAME_HOOK_SMEM_SLACK, value s in 1..1024: the tensor-core launch plans
+ *     keep s bytes for aligning the kernel's dynamic shared memory instead
+ *     of the padding that game_create's probe found (1024 gives the plans of
+ *     a device whose shared memory needs the full alignment: the large
+ *     classification plan then reads its targets from global memory instead
+ *     of staging them); 0 returns to the probed padding. A slack below the
+ *     real padding makes the kernel end before touching shared memory and
+ *     the call report GAME_ECUDA.
  * Returns GAME_EINVAL for an unknown hook or a value out of range. */
 #define GAME_HOOK_FAIL_ALLOC 1
 #define GAME_HOOK_STALL_NS 2
+#define GAME_HOOK_SMEM_SLACK 3
 int game_test_hook(int32_t hook, int64_t value);
 
 /* Releases the handle and all its device memory (NULL is accepted). */

@@ -763,6 +763,9 @@ int game_test_hook(int32_t hook, int64_t value) {
   } else if (hook == GAME_HOOK_STALL_NS) {
     if (value > 1000000000) return fail(GAME_EINVAL, "stall limited to 1 s");
     g_stall_ns.store((uint64_t)value);
+  } else if (hook == GAME_HOOK_SMEM_SLACK) {
+    if (value > 1024) return fail(GAME_EINVAL, "slack limited to 1024 bytes");
+    set_smem_slack_override((int)value);
   } else {
     return fail(GAME_EINVAL, "unknown hook");
   }

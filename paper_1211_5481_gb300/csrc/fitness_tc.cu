@@ -870,8 +870,13 @@ __global__ void smem_base_probe_kernel(int* out) {
 }
 }  // namespace
 
+static std::atomic<int> g_slack_override{0};
 void set_smem_base_pad(int pad) { g_base_pad = pad < 0 ? 1024 : (pad > 1024 ? 1024 : pad); }
-int smem_base_pad() { return g_base_pad; }
+int smem_base_pad() {
+  const int o = g_slack_override.load();
+  return o > 0 ? o : g_base_pad;
+}
+void set_smem_slack_override(int slack) { g_slack_override.store(slack); }
 void note_smem_base_pad(int pad) {
   static std::atomic<int> seen{-1};   // largest padding probed so far
   int cur = seen.load();

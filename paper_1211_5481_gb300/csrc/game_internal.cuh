@@ -107,6 +107,8 @@ void set_smem_base_pad(int pad);
 int smem_base_pad();
 // records a probe's result: the largest padding any probe has found so far
 void note_smem_base_pad(int pad);
+// test hook: plans keep `slack` bytes (1..1024) whatever the probes found; 0 off
+void set_smem_slack_override(int slack);
 // writes the probe's padding (0..1023) to *out (device memory) on stream st
 cudaError_t launch_smem_base_probe(int* out, cudaStream_t st);
 TcPlan plan_tc_pair(const Shape& s, int P, int num_sms);

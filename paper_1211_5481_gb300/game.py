@@ -37,6 +37,7 @@ GAME_SEL_RANKING = 1
 GAME_SEL_ROULETTE = 2
 GAME_HOOK_FAIL_ALLOC = 1
 GAME_HOOK_STALL_NS = 2
+GAME_HOOK_SMEM_SLACK = 3
 GAME_KERNEL_FP32 = 1
 GAME_KERNEL_TC = 2
 GAME_KERNEL_TC_PAIR = 3
@@ -365,7 +366,9 @@ def game_sync(h):
 def game_test_hook(hook: int, value: int):
     """Arms a test hook (GAME_HOOK_FAIL_ALLOC: the value-th device
     allocation from now fails; GAME_HOOK_STALL_NS: the next tensor-core
-    fitness launch runs into an expired wait after value ns; 0 = off)."""
+    fitness launch runs into an expired wait after value ns;
+    GAME_HOOK_SMEM_SLACK: tensor-core plans keep value bytes of alignment
+    slack; 0 = off)."""
     _check(load().game_test_hook(hook, value))
 
 

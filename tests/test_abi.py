@@ -235,6 +235,8 @@ def test_test_hook_refusals():
     assert lib.game_test_hook(99, 1) == game.GAME_EINVAL
     assert lib.game_test_hook(game.GAME_HOOK_FAIL_ALLOC, -1) == game.GAME_EINVAL
     assert lib.game_test_hook(game.GAME_HOOK_STALL_NS, 2_000_000_000) == game.GAME_EINVAL
+    assert lib.game_test_hook(game.GAME_HOOK_SMEM_SLACK, 1025) == game.GAME_EINVAL
     assert lib.game_last_error()
     assert lib.game_test_hook(game.GAME_HOOK_FAIL_ALLOC, 0) == game.GAME_OK
     assert lib.game_test_hook(game.GAME_HOOK_STALL_NS, 0) == game.GAME_OK
+    assert lib.game_test_hook(game.GAME_HOOK_SMEM_SLACK, 0) == game.GAME_OK

@@ -184,3 +184,31 @@ def test_create_rejects_bad_data(dev):
     y[0] = np.inf
     with pytest.raises(game.GameError):
         game.Game(pr.X, y, 3, CHEB, P=10)
+
+
+def test_staged_targets_bit_identical(dev):
+    """With features read from L2 (BF16, degree 8, 256-pattern tiles) the plan
+    stages each tile's targets in shared memory when the probe found the
+    dynamic shared memory aligned, and reads them from global memory when the
+    plan must keep the full 1 KB alignment slack (forced here with the test
+    hook). Only where the same FP32 targets are read from differs, so the
+    fitness is identical bit for bit; the plan's shared memory shows that
+    both paths ran."""
+    pr = dg.regression(77, 6000, 32, 4, 0.05, degree=8, basis=CHEB)
+    pop = dg.random_population(5, 256, pr.K)
+    with game.Game(pr.X, pr.y, 8, CHEB, P=256, precision=game.GAME_PREC_BF16) as g:
+        plan_probe = g.plan()
+        f_probe = g.eval_fitness(pop)
+        game.game_test_hook(game.GAME_HOOK_SMEM_SLACK, 1024)
+        try:
+            plan_slack = g.plan()
+            f_slack = g.eval_fitness(pop)
+        finally:
+            game.game_test_hook(game.GAME_HOOK_SMEM_SLACK, 0)
+        assert g.plan() == plan_probe
+    assert plan_probe["kernel"] == plan_slack["kernel"] == "fitness_tc_kernel"
+    assert plan_probe["tile"] == plan_slack["tile"] == 256 and plan_probe["staged"] == 0
+    # 2 KB of staged targets against 1 KB of slack: the probed plan is 1 KB
+    # larger when the probe found the base aligned (else the plans agree)
+    assert plan_probe["smem"] - plan_slack["smem"] in (0, 1024)
+    np.testing.assert_array_equal(f_probe, f_slack)

@@ -411,9 +411,12 @@ typedef struct {
  * (elitism, tournament, pc, pm, sigma, immigrants; its P, precision, seed,
  * rescore_top and stop threshold are ignored). tiles: the pattern-tile width
  * of each run's fitness items (32, 64, 128 or 256; NULL = choose): with
- * autotune != 0 the widths are timed per group of runs with the same
- * K-block count class and chromosome-tile count and the fastest kept, else
- * the widest that fits. Fitness values depend on the tile width in their
+ * autotune != 0, starting from the widest width that fits every run, each
+ * group of runs with the same K-block count class, widest width and
+ * chromosome-tile count is tried at its other widths while the whole
+ * fitness launch is timed, and
+ * a width kept when that launch gets at least 0.5% faster; with autotune ==
+ * 0 the widest that fits. Fitness values depend on the tile width in their
  * last bits (FP32 sums inside a tile): pass the widths game_batch_get_tiles
  * returns to reproduce a run exactly. Validation as game_create per run
  * (GAME_EINVAL naming the run), plus K - 1 <= 2048 and N <= 256; batched

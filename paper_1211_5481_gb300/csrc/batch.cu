@@ -13,8 +13,8 @@
 // The fitness of all runs is one persistent tensor-core launch over
 // (run, pattern tile) items (batch_tc.cu). The tile width BN of each run is
 // given by the caller, or picked per (K-block count, chromosome-tile count)
-// bucket by timing the bucket's items at every feasible width (the
-// autotuner), or by the largest feasible width. Fitness values depend on BN
+// bucket by timing the whole launch with the bucket at every feasible width
+// (the autotuner), or is the largest feasible width. Fitness values depend on BN
 // in their last bits (the FP32 sums inside a tile), so a run is reproducible
 // for a given tile choice; game_batch_get_tiles returns the choice.
 #include <algorithm>
@@ -260,9 +260,8 @@ void fill_run(const game_batch* b, int r, BatchRun& R) {
 }
 
 // Builds the fitness launch for the runs in `which` at the current tile
-// widths: run descriptors (with partial-row bases), items, a greedy
-// longest-first assignment of items to CTAs (each CTA's list then sorted by
-// run and tile), and the shared-memory plan. Uploads through the stream.
+// widths: run descriptors (with partial-row bases), the item list in
+// schedule order, and the shared-memory plan. Uploads through the stream.
 int build_launch(game_batch* b, const std::vector<int>& which) {
   std::vector<BatchRun> runs(b->R);
   for (int r = 0; r < b->R; ++r) fill_run(b, r, runs[r]);
@@ -455,48 +454,74 @@ int time_fitness(game_batch* b, int reps, double* ms) {
   return rc;
 }
 
-// The autotuner: runs bucketed by (K-block count class, chromosome tiles);
-// per bucket every width feasible for all its runs is timed on the bucket's
-// items alone (the pack of the current population comes first, so the
-// operands are real), and the fastest kept.
+// The autotuner: runs bucketed by (K-block count class, widest feasible
+// width, chromosome tiles).
+// It starts from the widest feasible width of every run and, bucket by
+// bucket (most work first), times the whole launch with the bucket at each
+// other width it fits, keeping a width only when the launch gets at least
+// 0.5% faster. The whole launch is timed, not the bucket alone: items share
+// the SMs through one work counter, so what counts is a bucket's throughput
+// next to the others; alone, a small bucket underfills the GPU and narrow
+// tiles win on latency. The pack of the current population comes first, so
+// the operands are real.
 int autotune(game_batch* b) {
   std::vector<std::vector<int>> buckets;
   std::vector<std::pair<int, int>> keys;
+  std::vector<double> work;
   for (int r = 0; r < b->R; ++r) {
     int kc = 0;
     while ((1 << kc) < b->KB[r]) ++kc;
-    const std::pair<int, int> key(kc, b->C[r]);
+    // the widest feasible width is part of the key: one K-block class can
+    // hold runs that fit 128-pattern tiles and runs that fit only 64
+    const int widest = heuristic_bn(b->shape[r], b->KB[r]);
+    const std::pair<int, int> key(kc * 512 + widest, b->C[r]);
     size_t i = 0;
     while (i < keys.size() && keys[i] != key) ++i;
     if (i == keys.size()) {
       keys.push_back(key);
       buckets.emplace_back();
+      work.push_back(0.0);
     }
     buckets[i].push_back(r);
+    work[i] += (double)b->shape[r].M * b->KB[r] * b->C[r];
   }
-  int rc = enqueue_pack(b, b->cur);
-  if (rc) return rc;
-  for (const auto& runs : buckets) {
-    int best_bn = 0;
-    double best = 1e300;
+  std::vector<int> order(buckets.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+  std::vector<int> all(b->R);
+  for (int r = 0; r < b->R; ++r) all[r] = r;
+  for (int r = 0; r < b->R; ++r) b->BN[r] = heuristic_bn(b->shape[r], b->KB[r]);
+  int rc = build_launch(b, all);
+  if (!rc) rc = enqueue_pack(b, b->cur);
+  double ms = 0.0;
+  if (!rc) rc = time_fitness(b, 8, &ms);   // clocks up before anything is compared
+  for (int i : order) {
+    if (rc) break;
+    const std::vector<int>& runs = buckets[i];
+    const int cur_bn = b->BN[runs[0]];
+    int best_bn = cur_bn;
+    // the current widths are timed again next to each bucket's trials, so
+    // a drift of the clocks between buckets is not read as a gain
+    double best = 0.0;
+    rc = build_launch(b, all);
+    if (!rc) rc = time_fitness(b, 4, &best);
     for (int bn : {256, 128, 64, 32}) {
-      bool ok = true;
+      if (rc) break;
+      bool ok = bn != cur_bn;
       for (int r : runs) ok = ok && tile_fits(b->shape[r], b->KB[r], bn);
       if (!ok) continue;
       for (int r : runs) b->BN[r] = bn;
-      rc = build_launch(b, runs);
-      if (rc) return rc;
-      double ms = 0.0;
-      rc = time_fitness(b, 3, &ms);
-      if (rc) return rc;
-      if (ms < best) {
+      rc = build_launch(b, all);
+      if (!rc) rc = time_fitness(b, 4, &ms);
+      if (rc) break;
+      if (ms < best * 0.995) {
         best = ms;
         best_bn = bn;
       }
     }
     for (int r : runs) b->BN[r] = best_bn;
   }
-  return GAME_OK;
+  return rc;
 }
 
 int capture(game_batch* b, int parity) {

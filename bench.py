@@ -89,7 +89,7 @@ def parse():
 # dram__bytes_write.sum of one ncu capture), per workload and form, with the
 # digest of the kernel sources the capture ran: reported only while the
 # sources are unchanged (null once the kernel has changed since).
-NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): (132.64e6 + 3.02e6, "faf99fe9f6e36447")}
+NCU_TRAFFIC = {("M1000000_N32_cheb8_P1024_cls", "bf16"): (132.64e6 + 3.21e6, "014c5a2ac9e5a2bc")}
 KERNEL_SOURCES = ("fitness_tc.cu", "fitness_tc2.cu", "tc_common.cuh", "tc_ptx.cuh",
                   "basis.cuh")
 

@@ -224,15 +224,25 @@ bool is_dev(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Shared-memory bytes of one item of run r at tile width bn.
-bool tile_fits(const Shape& s, int KB, int bn) {
-  (void)s;
-  return KB * bn * 128 <= kPhiBudget;
+// Expansion K-block slots of an item with KB K-blocks, C chromosome tiles
+// and tile width bn: one per K-block when they fit the budget; else, for
+// 256-pattern tiles of a single chromosome tile, a ring of kRingSlots (one
+// thread per pattern row fills the K-blocks in order, and the one
+// accumulator group releases each K-block as soon as its MMAs are done);
+// else 0 (the width does not fit).
+constexpr int kRingSlots = 4;   // a power of two: the kernel maps K-block kb to kb & 3
+static_assert(kRingSlots * 256 * 128 <= kPhiBudget, "ring slots exceed the expansion budget");
+int phi_slots(int KB, int C, int bn) {
+  if (KB * bn * 128 <= kPhiBudget) return KB;
+  if (bn == 256 && C == 1) return kRingSlots;
+  return 0;
 }
 
-int heuristic_bn(const Shape& s, int KB) {
+bool tile_fits(int KB, int C, int bn) { return phi_slots(KB, C, bn) > 0; }
+
+int heuristic_bn(int KB, int C) {
   for (int bn : {256, 128, 64, 32})
-    if (tile_fits(s, KB, bn)) return bn;
+    if (tile_fits(KB, C, bn)) return bn;
   return 0;
 }
 
@@ -273,9 +283,11 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
     BatchRun& R = runs[r];
     R.part_base = part_total;
     part_total += (int64_t)R.ntiles * R.Ppad;
-    KBmax = std::max(KBmax, R.KB);
+    const int RK = phi_slots(R.KB, R.C, R.BN);
+    if (RK < 1) return bfail(GAME_EINVAL, "tile width does not fit");
+    KBmax = std::max(KBmax, RK);   // barrier pairs: one per slot
     set_max = std::max(set_max, std::min(R.C, 256 / R.BN) * R.BN);
-    phi_bytes = std::max(phi_bytes, R.KB * R.BN * 128);
+    phi_bytes = std::max(phi_bytes, RK * R.BN * 128);
     // cycles per item, roughly: the expansion (64 BN values per K-block at
     // about 4 per cycle, sincosf once per feature for the trigonometric
     // basis), the MMAs (about 2.5 BN per K-block and chromosome tile), the
@@ -349,6 +361,7 @@ int build_launch(game_batch* b, const std::vector<int>& which) {
     I.nmma_last = R.nmma_last;
     I.valid = (int)std::min<int64_t>(R.BN, R.M - I.m0);
     I.CG = std::min(R.C, 256 / R.BN);
+    I.RK = phi_slots(R.KB, R.C, R.BN);
   }
   BCK(cudaMemcpyAsync(b->runs_d, runs.data(), sizeof(BatchRun) * b->R, cudaMemcpyHostToDevice,
                       b->st));
@@ -473,7 +486,7 @@ int autotune(game_batch* b) {
     while ((1 << kc) < b->KB[r]) ++kc;
     // the widest feasible width is part of the key: one K-block class can
     // hold runs that fit 128-pattern tiles and runs that fit only 64
-    const int widest = heuristic_bn(b->shape[r], b->KB[r]);
+    const int widest = heuristic_bn(b->KB[r], b->C[r]);
     const std::pair<int, int> key(kc * 512 + widest, b->C[r]);
     size_t i = 0;
     while (i < keys.size() && keys[i] != key) ++i;
@@ -490,7 +503,7 @@ int autotune(game_batch* b) {
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
   std::vector<int> all(b->R);
   for (int r = 0; r < b->R; ++r) all[r] = r;
-  for (int r = 0; r < b->R; ++r) b->BN[r] = heuristic_bn(b->shape[r], b->KB[r]);
+  for (int r = 0; r < b->R; ++r) b->BN[r] = heuristic_bn(b->KB[r], b->C[r]);
   int rc = build_launch(b, all);
   if (!rc) rc = enqueue_pack(b, b->cur);
   double ms = 0.0;
@@ -508,7 +521,7 @@ int autotune(game_batch* b) {
     for (int bn : {256, 128, 64, 32}) {
       if (rc) break;
       bool ok = bn != cur_bn;
-      for (int r : runs) ok = ok && tile_fits(b->shape[r], b->KB[r], bn);
+      for (int r : runs) ok = ok && tile_fits(b->KB[r], b->C[r], bn);
       if (!ok) continue;
       for (int r : runs) b->BN[r] = bn;
       rc = build_launch(b, all);
@@ -628,18 +641,19 @@ int game_batch_create(const game_run_desc* runs, int32_t R, const game_params* p
     s.Kp = s.K - 1;
     if (d.P < p.elitism + p.immigrants + 2 || d.P > (1 << 20))
       return bail(bfail(GAME_EINVAL, "run " + std::to_string(r) + ": bad population size"));
-    if (!tile_fits(s, KB, 32))
+    const int C = (d.P + 127) / 128;
+    if (!tile_fits(KB, C, 32))
       return bail(bfail(GAME_EINVAL, "run " + std::to_string(r) + ": too many features"));
     b->shape.push_back(s);
     b->P.push_back(d.P);
-    b->C.push_back((d.P + 127) / 128);
+    b->C.push_back(C);
     b->Ppad.push_back(b->C.back() * 128);
     b->KB.push_back(KB);
     b->seed.push_back(d.seed);
-    int bn = tiles ? tiles[r] : heuristic_bn(s, KB);
+    int bn = tiles ? tiles[r] : heuristic_bn(KB, C);
     if (bn != 256 && bn != 128 && bn != 64 && bn != 32)
       return bail(bfail(GAME_EINVAL, "run " + std::to_string(r) + ": tile width not 32..256"));
-    if (!tile_fits(s, KB, bn))
+    if (!tile_fits(KB, C, bn))
       return bail(bfail(GAME_EINVAL, "run " + std::to_string(r) + ": tile too wide"));
     b->BN.push_back(bn);
     b->off_X.push_back(nX);

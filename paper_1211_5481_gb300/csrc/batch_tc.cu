@@ -76,20 +76,28 @@ __host__ __device__ inline BSmem bsmem_plan(int phi_bytes, int KBmax) {
 
 // The expansion role's state carried from item to item, and its constants.
 //
-// Every expansion thread arrives once per item on every K-block's phi_full
+// K-block kb of an item lives in slot kb (ring items: kb mod RK, RK a power
+// of two).
+// Every expansion thread arrives once per K-block on its slot's phi_full
 // barrier (count 256), after its last store into that K-block (at once for a
 // K-block it does not write). Before it stores into, or arrives on, K-block
 // kb of an item it awaits the phi_free phases (the MMAs' release) of every
-// K-block <= kb that it arrived on in an earlier item and has not awaited
+// slot <= kb that it arrived on in an earlier item and has not awaited
 // since. A thread's stores and arrivals go in increasing K-block order and
 // the MMA issuer releases K-blocks in increasing order, so this costs no more
 // than awaiting kb alone, and every phase is awaited exactly once, in order,
 // which keeps the parity bits exact. The current item's own arrivals join
 // the pending set only when the item ends: its phi_free phases come after
 // the MMAs of all its chromosome tiles, which need all its K-blocks.
+// Ring items (RK < KB: 256-pattern tiles of one chromosome tile, so one
+// thread per row and one accumulator group) reuse slots within the item:
+// there an arrival joins the pending set at once, since the MMAs release a
+// K-block as soon as they have used it, and before its next use the thread
+// awaits that slot alone (other slots' phases may be awaited later, when
+// their own K-blocks come; each slot holds one pending phase at most).
 struct ExpState {
-  uint32_t pending;    // bit kb: arrived on phi_full[kb] in an earlier item, phi_free phase not yet awaited
-  uint32_t free_par;   // bit kb: parity of the next phi_free[kb] phase
+  uint32_t pending;    // bit k: arrived on phi_full[k], phi_free phase not yet awaited
+  uint32_t free_par;   // bit k: parity of the next phi_free[k] phase
   int dead;            // a wait failed (time limit or another role's abort)
 };
 struct ExpEnv {
@@ -119,24 +127,43 @@ struct RowCursor {
   ExpState& es;
   const ExpEnv& env;
   int BN, r0, colmax;   // colmax = KB * 64
+  int rmask;            // K-block kb in slot kb & rmask (all ones unless a ring)
+  bool ring;            // the item reuses slots (RK < KB, RK a power of two)
   int next_arr;         // next K-block to arrive on
-  int awaited;          // previous phases of K-blocks <= awaited are awaited
+  int awaited;          // the phases K-block `awaited` (and every lower one) needs are awaited
 
-  __device__ __forceinline__ void await_upto(int kb) {
-    const uint32_t m = es.pending & (kb >= 31 ? 0xFFFFFFFFu : ((2u << kb) - 1u));
+  // before the first store into, or arrival on, K-block kb
+  __device__ __forceinline__ void await_for(int kb) {
+    uint32_t m = ring ? 1u << (kb & rmask) : (kb >= 31 ? 0xFFFFFFFFu : ((2u << kb) - 1u));
+    m &= es.pending;
     if (m != 0u) await_mask(es, env, m);
     awaited = kb;
   }
-  __device__ __forceinline__ void arrive(int kb) { ptx::mbar_arrive(env.phi_full0 + 8u * (uint32_t)kb); }
+  __device__ __forceinline__ void arrive(int kb) {
+    const int sl = kb & rmask;
+    ptx::mbar_arrive(env.phi_full0 + 8u * (uint32_t)sl);
+    if (ring) es.pending |= 1u << sl;
+  }
   // after the item's last arrival: its K-blocks [0, KB) join the pending set
+  // (ring items: each at its arrival)
   __device__ __forceinline__ void end_item(int KB) {
-    es.pending |= KB >= 32 ? 0xFFFFFFFFu : ((1u << KB) - 1u);
+    if (!ring) es.pending |= KB >= 32 ? 0xFFFFFFFFu : ((1u << KB) - 1u);
   }
   // arrive on K-blocks [next_arr, kbe)
   __device__ __forceinline__ void arrive_below(int kbe) {
     if (kbe <= next_arr || es.dead) return;
+    if (ring) {
+      ptx::fence_proxy_async_smem();
+      for (int k = next_arr; k < kbe; ++k) {
+        if (k > awaited) await_for(k);
+        if (es.dead) return;
+        arrive(k);
+        next_arr = k + 1;
+      }
+      return;
+    }
     if (kbe - 1 > awaited) {
-      await_upto(kbe - 1);
+      await_for(kbe - 1);
       if (es.dead) return;
     }
     ptx::fence_proxy_async_smem();
@@ -147,10 +174,10 @@ struct RowCursor {
     if (col >= colmax || es.dead) return;
     const int kb = col >> 6;
     if (kb > awaited) {
-      await_upto(kb);
+      await_for(kb);
       if (es.dead) return;
     }
-    ptx::st_shared_v4(env.phi + (uint32_t)(kb * BN * 128 + r0 * 128) +
+    ptx::st_shared_v4(env.phi + (uint32_t)((kb & rmask) * BN * 128 + r0 * 128) +
                           (uint32_t)((((col >> 3) & 7) ^ (r0 & 7)) << 4), val);
     if (((col + 8) & 63) == 0) {
       ptx::fence_proxy_async_smem();
@@ -208,12 +235,12 @@ __device__ __forceinline__ void issue_group(const float* xp, int i0, int N, uint
 // inlined: each (basis, degree) gets its own register allocation.
 template <int BASIS, int D>
 __device__ __noinline__ ExpState expand_item(ExpState es, const ExpEnv env, const float* xp,
-                                             int N, int KB, int BN, int r0, int q0, int QS,
-                                             int bt) {
+                                             int N, int KB, int RK, int BN, int r0, int q0,
+                                             int QS, int bt) {
   using FG = FeatureGroup<BASIS, D>;
   constexpr int U = FG::U, UF = FG::U * FG::F, UG = FG::U * FG::G;
   constexpr int PD = kRing / UF;   // UF divides 16
-  RowCursor rc{es, env, BN, r0, KB * 64, 0, -1};
+  RowCursor rc{es, env, BN, r0, KB * 64, RK < KB ? RK - 1 : -1, RK < KB, 0, -1};
   const int ng = (N + FG::F - 1) / FG::F;
   const int gb = q0 * ng / QS, ge = (q0 + 1) * ng / QS;
   const int cs = gb * FG::G < rc.colmax ? gb * FG::G : rc.colmax;
@@ -256,7 +283,7 @@ __device__ __noinline__ ExpState expand_item(ExpState es, const ExpEnv env, cons
 __device__ __noinline__ ExpState expand_item_generic(ExpState es, const ExpEnv env,
                                                      const float* xp, const BatchItem R, int r0,
                                                      int q0, int QS) {
-  RowCursor rc{es, env, R.BN, r0, R.KB * 64, 0, -1};
+  RowCursor rc{es, env, R.BN, r0, R.KB * 64, R.RK < R.KB ? R.RK - 1 : -1, R.RK < R.KB, 0, -1};
   const int CPT = 8 / QS;
   for (int kb = 0; kb < R.KB && !es.dead; ++kb) {
     for (int qd = q0 * CPT; qd < (q0 + 1) * CPT; ++qd) {
@@ -274,18 +301,18 @@ template <int BASIS>
 __device__ __forceinline__ ExpState expand_dispatch(ExpState es, const ExpEnv& env,
                                                     const float* xp, const BatchItem& R, int r0,
                                                     int q0, int QS, int bt) {
-  const int N = R.N, KB = R.KB, BN = R.BN;
+  const int N = R.N, KB = R.KB, RK = R.RK, BN = R.BN;
   switch (R.d) {
-    case 1: return expand_item<BASIS, 1>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 2: return expand_item<BASIS, 2>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 3: return expand_item<BASIS, 3>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 4: return expand_item<BASIS, 4>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 5: return expand_item<BASIS, 5>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 6: return expand_item<BASIS, 6>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 7: return expand_item<BASIS, 7>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 8: return expand_item<BASIS, 8>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 9: return expand_item<BASIS, 9>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
-    case 10: return expand_item<BASIS, 10>(es, env, xp, N, KB, BN, r0, q0, QS, bt);
+    case 1: return expand_item<BASIS, 1>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 2: return expand_item<BASIS, 2>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 3: return expand_item<BASIS, 3>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 4: return expand_item<BASIS, 4>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 5: return expand_item<BASIS, 5>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 6: return expand_item<BASIS, 6>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 7: return expand_item<BASIS, 7>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 8: return expand_item<BASIS, 8>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 9: return expand_item<BASIS, 9>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
+    case 10: return expand_item<BASIS, 10>(es, env, xp, N, KB, RK, BN, r0, q0, QS, bt);
     default: return expand_item_generic(es, env, xp, R, r0, q0, QS);
   }
 }
@@ -450,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
       const uint32_t phi_full0 = ptx::smem_addr(phi_full), phi_free0 = ptx::smem_addr(phi_free);
       const uint32_t acc_full0 = ptx::smem_addr(acc_full), acc_empty0 = ptx::smem_addr(acc_empty);
       uint32_t s = 0, ph = 0, acc_it = 0;
-      uint32_t full_par = 0;   // bit kb: parity of the next phi_full[kb] phase
+      uint32_t full_par = 0;   // bit k: parity of the next phi_full[k] phase
       bool ok = true;
       BatchItem nxt;
       int idx_n = iq.pop();
@@ -462,9 +489,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
         const int KB = R.KB, C = R.C, BN = R.BN, CG = R.CG, nlast = R.nmma_last;
         const uint32_t idesc = ptx::idesc_bf16_f32(128, BN);
         const uint32_t b_step = (uint32_t)(BN * 128) >> 4;
-        auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int nm) {
+        const int rmask = R.RK < KB ? R.RK - 1 : -1;   // K-block kb in slot kb & rmask
+        auto kblock = [&](uint32_t d_tmem, uint32_t st, int kb, int slot, int nm) {
           const uint64_t ad = adesc0 + st * a_step;
-          const uint64_t bd = bdesc0 + (uint32_t)kb * b_step;
+          const uint64_t bd = bdesc0 + (uint32_t)slot * b_step;
           for (int kk = 0; kk < nm; ++kk)
             ptx::mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0);
         };
@@ -472,7 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
         // side in one accumulator set; per group the K-blocks are the outer
         // loop, so with one group (C <= 256 / BN) a K-block is released as
         // soon as every tile has used it and the next item's expansion
-        // follows this item's MMAs K-block by K-block.
+        // follows this item's MMAs K-block by K-block. K-block kb sits in
+        // slot kb (ring items, one group by construction: kb mod RK, the
+        // expansion refilling slots within the item).
         for (int c0 = 0; c0 < C && ok; c0 += CG) {
           const int c1 = c0 + CG < C ? c0 + CG : C;
           const bool last_group = c1 == C;
@@ -482,25 +512,27 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
           ptx::tc_fence_after();
           const uint32_t d_set = tmem + set * (uint32_t)a.set_cols;
           for (int kb = 0; kb < KB && ok; ++kb) {
-            if (c0 == 0) ok = wait_bar(phi_full0 + 8 * kb, (full_par >> kb) & 1u, abort_flag,
-                                       a.status);
+            const int slot = kb & rmask;
+            if (c0 == 0) {
+              ok = wait_bar(phi_full0 + 8 * slot, (full_par >> slot) & 1u, abort_flag, a.status);
+              full_par ^= 1u << slot;
+            }
             for (int c = c0; c < c1 && ok; ++c) {
               ok = wait_bar(a_full0 + 8 * s, ph, abort_flag, a.status);
               if (!ok) break;
-              kblock(d_set + (uint32_t)((c - c0) * BN), s, kb, kb == KB - 1 ? nlast : 4);
+              kblock(d_set + (uint32_t)((c - c0) * BN), s, kb, slot, kb == KB - 1 ? nlast : 4);
               ptx::mma_commit(a_empty0 + 8 * s);
               if (++s == (uint32_t)kStages) {
                 s = 0;
                 ph ^= 1;
               }
             }
-            if (ok && last_group) ptx::mma_commit(phi_free0 + 8 * kb);
+            if (ok && last_group) ptx::mma_commit(phi_free0 + 8 * slot);
           }
           if (!ok) break;
           ptx::mma_commit(acc_full0 + 8 * set);
           ++acc_it;
         }
-        full_par ^= (KB >= 32) ? 0xFFFFFFFFu : ((1u << KB) - 1u);
       }
       ptx::mma_commit(ptx::smem_addr(drain));
       wait_bar_drain(ptx::smem_addr(drain), 0, a.status);
@@ -612,11 +644,11 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_batch_kernel(const BatchA
     }
   } else if (warp >= kBasisWarp0) {
     // ---------------- expansion (basis) ----------------
-    // K-block kb of an item sits at kb * BN * 128, so when BN changes from one
-    // item to the next a new K-block can overlap any K-block of the previous
+    // Slot k of an item sits at k * BN * 128, so when BN changes from one
+    // item to the next a new slot can overlap any slot of the previous
     // layout: then every outstanding phi_free phase is awaited before the
-    // first store (each CTA's items are sorted by tile width, so this happens
-    // at most three times).
+    // first store (the item list runs by tile width, so this happens at most
+    // three times per CTA).
     const int bt = threadIdx.x - kBasisWarp0 * 32;
     ExpState es{0u, 0u, 0};
     const ExpEnv env{ptx::smem_addr(phi), ptx::smem_addr(ring), ptx::smem_addr(phi_full),

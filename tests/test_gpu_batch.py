@@ -187,3 +187,44 @@ def test_batch_every_degree_matches_cpu_model(tiles):
                 want, tol = model("bf16", X, y, pop, d, basis)
                 err = np.abs(fit - want)
                 assert np.all(err <= tol), (r, DEGREE_RUNS[r], float((err / tol).max()))
+
+
+# Runs of one chromosome tile whose contraction is longer than four 256-pattern
+# K-blocks fit: 256-pattern tiles whose K-blocks cycle through a ring of four
+# expansion slots (K' from 320 to 2048, templated and generic degrees, ragged
+# tails), next to runs that use one slot per K-block at 256, 128 and 64
+# patterns, so that the kernel passes between ring and plain items and
+# between widths.
+RING_RUNS = [
+    (1500, 40, 8, CHEB, 100, 301),     # K' = 320: 5 K-blocks
+    (2100, 33, 10, TRIG, 128, 302),    # 660: 11
+    (900, 70, 12, CHEB, 64, 303),      # 840: 14, generic generator
+    (700, 90, 11, TRIG, 17, 304),      # 1980: 31, generic
+    (600, 128, 16, CHEB, 50, 305),     # 2048: 32, generic
+    (1201, 96, 3, TRIG, 96, 306),      # 576: 9
+    (1200, 64, 4, CHEB, 120, 307),     # 256: 4 K-blocks, one slot each
+    (1000, 20, 9, TRIG, 200, 308),     # 360, two chromosome tiles: 128 patterns
+    (800, 60, 10, CHEB, 300, 309),     # 600, three tiles: 64 patterns
+]
+
+
+def test_batch_ring_items_match_cpu_model():
+    """Ring items against the CPU model of the BF16 form, element by element,
+    over two generations."""
+    from emulation import model
+    args, probs = [], []
+    for (M, N, d, basis, P, seed) in RING_RUNS:
+        pr = dg.regression(seed, M, N, min(d, 4), 0.05, degree=d, basis=basis)
+        X = (pr.X * np.float32(3.0 if basis == TRIG else 1.0)).astype(np.float32)
+        args.append((X, pr.y, d, basis, P, seed))
+        probs.append((X, pr.y, d, basis))
+    with game.Batch(args, autotune=False) as b:
+        assert b.tiles().tolist() == [256] * 7 + [128, 64]
+        for gen in range(2):
+            if gen:
+                b.generation()
+            for r, (X, y, d, basis) in enumerate(probs):
+                pop, fit, _ = b.run(r)
+                want, tol = model("bf16", X, y, pop, d, basis)
+                err = np.abs(fit - want)
+                assert np.all(err <= tol), (r, RING_RUNS[r], float((err / tol).max()))

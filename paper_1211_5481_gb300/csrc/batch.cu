@@ -225,16 +225,20 @@ bool is_dev(const void* p) {
 }
 
 // Expansion K-block slots of an item with KB K-blocks, C chromosome tiles
-// and tile width bn: one per K-block when they fit the budget; else, for
-// 256-pattern tiles of a single chromosome tile, a ring of kRingSlots (one
-// thread per pattern row fills the K-blocks in order, and the one
-// accumulator group releases each K-block as soon as its MMAs are done);
-// else 0 (the width does not fit).
-constexpr int kRingSlots = 4;   // a power of two: the kernel maps K-block kb to kb & 3
-static_assert(kRingSlots * 256 * 128 <= kPhiBudget, "ring slots exceed the expansion budget");
+// and tile width bn: one per K-block when they fit the budget; else a ring
+// (K-block kb in slot kb & (slots - 1)) where the item's chromosome tiles
+// form one accumulator group, so the MMAs release each K-block as soon as
+// they have used it: 4 slots at 256 patterns (one thread per pattern row
+// fills the K-blocks in order), 8 at 128 patterns for at most 16 K-blocks
+// (two threads per row; each one's range then starts within the ring's
+// first pass, so the two fill side by side); else 0 (the width does not
+// fit).
+static_assert(4 * 256 * 128 <= kPhiBudget && 8 * 128 * 128 <= kPhiBudget,
+              "ring slots exceed the expansion budget");
 int phi_slots(int KB, int C, int bn) {
   if (KB * bn * 128 <= kPhiBudget) return KB;
-  if (bn == 256 && C == 1) return kRingSlots;
+  if (bn == 256 && C == 1) return 4;
+  if (bn == 128 && C <= 2 && KB <= 16) return 8;
   return 0;
 }
 

@@ -89,12 +89,14 @@ __host__ __device__ inline BSmem bsmem_plan(int phi_bytes, int KBmax) {
 // which keeps the parity bits exact. The current item's own arrivals join
 // the pending set only when the item ends: its phi_free phases come after
 // the MMAs of all its chromosome tiles, which need all its K-blocks.
-// Ring items (RK < KB: 256-pattern tiles of one chromosome tile, so one
-// thread per row and one accumulator group) reuse slots within the item:
+// Ring items (RK < KB, one accumulator group) reuse slots within the item:
 // there an arrival joins the pending set at once, since the MMAs release a
-// K-block as soon as they have used it, and before its next use the thread
-// awaits that slot alone (other slots' phases may be awaited later, when
-// their own K-blocks come; each slot holds one pending phase at most).
+// K-block as soon as they have used it, and before its next use (a store or
+// an arrival) the thread awaits that slot alone (other slots' phases may be
+// awaited later, when their own K-blocks come; each slot holds one pending
+// phase at most). With several threads per row, a thread whose range starts
+// past the ring's first pass waits there for the MMAs of the row's earlier
+// K-blocks: slower, never stuck, as the others never wait on it.
 struct ExpState {
   uint32_t pending;    // bit k: arrived on phi_full[k], phi_free phase not yet awaited
   uint32_t free_par;   // bit k: parity of the next phi_free[k] phase

@@ -151,8 +151,9 @@ struct alignas(16) BatchItem {
   int64_t m0;               // first pattern of the tile
   int N, d, basis, Kp, KB, C, BN, nmma_last, valid;
   int CG;                   // chromosome tiles per accumulator set: min(C, 256 / BN)
-  int RK;                   // expansion K-block slots: KB, or fewer (a ring; K-block kb in
-                            // slot kb % RK) for 256-pattern tiles of one chromosome tile
+  int RK;                   // expansion K-block slots: KB, or fewer, a power of two (a ring:
+                            // K-block kb in slot kb & (RK - 1)) when the item's chromosome
+                            // tiles form one accumulator group
   int pad1;
 };
 struct BatchArgs {

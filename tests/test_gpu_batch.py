@@ -189,12 +189,13 @@ def test_batch_every_degree_matches_cpu_model(tiles):
                 assert np.all(err <= tol), (r, DEGREE_RUNS[r], float((err / tol).max()))
 
 
-# Runs of one chromosome tile whose contraction is longer than four 256-pattern
-# K-blocks fit: 256-pattern tiles whose K-blocks cycle through a ring of four
-# expansion slots (K' from 320 to 2048, templated and generic degrees, ragged
-# tails), next to runs that use one slot per K-block at 256, 128 and 64
-# patterns, so that the kernel passes between ring and plain items and
-# between widths.
+# Runs whose contraction is longer than their tile's expansion slots hold:
+# one chromosome tile at 256 patterns, K-blocks cycling through a ring of four
+# slots (K' from 320 to 2048, templated and generic degrees, ragged tails);
+# two chromosome tiles at 128 patterns with up to 16 K-blocks, a ring of
+# eight slots filled by two threads per row; next to runs that use one slot
+# per K-block at 256, 128 and 64 patterns, so that the kernel passes between
+# ring and plain items and between widths.
 RING_RUNS = [
     (1500, 40, 8, CHEB, 100, 301),     # K' = 320: 5 K-blocks
     (2100, 33, 10, TRIG, 128, 302),    # 660: 11
@@ -205,6 +206,9 @@ RING_RUNS = [
     (1200, 64, 4, CHEB, 120, 307),     # 256: 4 K-blocks, one slot each
     (1000, 20, 9, TRIG, 200, 308),     # 360, two chromosome tiles: 128 patterns
     (800, 60, 10, CHEB, 300, 309),     # 600, three tiles: 64 patterns
+    (1100, 50, 7, TRIG, 256, 310),     # 700, two tiles: 11 K-blocks in 8 slots at 128
+    (900, 64, 8, TRIG, 140, 311),      # 1024, two tiles: 16 K-blocks in 8 slots
+    (700, 68, 8, TRIG, 150, 312),      # 1088, two tiles, 17 K-blocks: 64 patterns
 ]
 
 
@@ -219,7 +223,7 @@ def test_batch_ring_items_match_cpu_model():
         args.append((X, pr.y, d, basis, P, seed))
         probs.append((X, pr.y, d, basis))
     with game.Batch(args, autotune=False) as b:
-        assert b.tiles().tolist() == [256] * 7 + [128, 64]
+        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 64]
         for gen in range(2):
             if gen:
                 b.generation()

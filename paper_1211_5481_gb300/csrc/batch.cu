@@ -229,16 +229,17 @@ bool is_dev(const void* p) {
 // (K-block kb in slot kb & (slots - 1)) where the item's chromosome tiles
 // form one accumulator group, so the MMAs release each K-block as soon as
 // they have used it: 4 slots at 256 patterns (one thread per pattern row
-// fills the K-blocks in order), 8 at 128 patterns for at most 16 K-blocks
-// (two threads per row; each one's range then starts within the ring's
-// first pass, so the two fill side by side); else 0 (the width does not
-// fit).
+// fills the K-blocks in order), 8 at 128 patterns (two threads per row; up
+// to 16 K-blocks the second one's range starts within the ring's first
+// pass and the two fill side by side, beyond it waits there for the MMAs
+// of the row's first K-blocks, which still beats narrower tiles on the
+// 256-run workload); else 0 (the width does not fit).
 static_assert(4 * 256 * 128 <= kPhiBudget && 8 * 128 * 128 <= kPhiBudget,
               "ring slots exceed the expansion budget");
 int phi_slots(int KB, int C, int bn) {
   if (KB * bn * 128 <= kPhiBudget) return KB;
   if (bn == 256 && C == 1) return 4;
-  if (bn == 128 && C <= 2 && KB <= 16) return 8;
+  if (bn == 128 && C <= 2) return 8;
   return 0;
 }
 

@@ -192,10 +192,11 @@ def test_batch_every_degree_matches_cpu_model(tiles):
 # Runs whose contraction is longer than their tile's expansion slots hold:
 # one chromosome tile at 256 patterns, K-blocks cycling through a ring of four
 # slots (K' from 320 to 2048, templated and generic degrees, ragged tails);
-# two chromosome tiles at 128 patterns with up to 16 K-blocks, a ring of
-# eight slots filled by two threads per row; next to runs that use one slot
-# per K-block at 256, 128 and 64 patterns, so that the kernel passes between
-# ring and plain items and between widths.
+# two chromosome tiles at 128 patterns, a ring of eight slots filled by two
+# threads per row (beyond 16 K-blocks the second thread's range starts past
+# the ring's first pass); next to runs that use one slot per K-block at 256,
+# 128 and 64 patterns, so that the kernel passes between ring and plain
+# items and between widths.
 RING_RUNS = [
     (1500, 40, 8, CHEB, 100, 301),     # K' = 320: 5 K-blocks
     (2100, 33, 10, TRIG, 128, 302),    # 660: 11
@@ -208,7 +209,8 @@ RING_RUNS = [
     (800, 60, 10, CHEB, 300, 309),     # 600, three tiles: 64 patterns
     (1100, 50, 7, TRIG, 256, 310),     # 700, two tiles: 11 K-blocks in 8 slots at 128
     (900, 64, 8, TRIG, 140, 311),      # 1024, two tiles: 16 K-blocks in 8 slots
-    (700, 68, 8, TRIG, 150, 312),      # 1088, two tiles, 17 K-blocks: 64 patterns
+    (700, 68, 8, TRIG, 150, 312),      # 1088, two tiles: 17 K-blocks in 8 slots
+    (600, 128, 8, TRIG, 200, 313),     # 2048, two tiles: 32 K-blocks in 8 slots
 ]
 
 
@@ -223,7 +225,7 @@ def test_batch_ring_items_match_cpu_model():
         args.append((X, pr.y, d, basis, P, seed))
         probs.append((X, pr.y, d, basis))
     with game.Batch(args, autotune=False) as b:
-        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 64]
+        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 128, 128]
         for gen in range(2):
             if gen:
                 b.generation()

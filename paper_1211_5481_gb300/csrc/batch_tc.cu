@@ -14,9 +14,10 @@
 // them in the same order; each role loads its next item's record while it
 // works on the current one. The shared-memory regions are sized for the
 // largest item of the batch; within an item the layout follows the item's own
-// BN and K-block count. Because items use different numbers of K-blocks, the
-// phases of the per-K-block barriers are tracked as bit masks (one bit per
-// K-block, flipped at each use) instead of the item counter.
+// BN and its expansion slots (one per K-block, or a ring of RK slots). Because
+// items use different numbers of slots, the phases of the per-slot barriers
+// are tracked as bit masks (one bit per slot, flipped at each use) instead of
+// the item counter.
 //
 // Roles: warp 0 gene-block producer, warp 1 MMA issuer and TMEM owner, warp 2
 // scheduler and L2 prefetcher, warps 4-7 epilogue (targets staged in shared memory one item
@@ -96,7 +97,8 @@ __host__ __device__ inline BSmem bsmem_plan(int phi_bytes, int KBmax) {
 // awaited later, when their own K-blocks come; each slot holds one pending
 // phase at most). With several threads per row, a thread whose range starts
 // past the ring's first pass waits there for the MMAs of the row's earlier
-// K-blocks: slower, never stuck, as the others never wait on it.
+// K-blocks: slower, never stuck, as every wait is for the MMAs of a lower
+// K-block, whose arrivals come first in each thread's order.
 struct ExpState {
   uint32_t pending;    // bit k: arrived on phi_full[k], phi_free phase not yet awaited
   uint32_t free_par;   // bit k: parity of the next phi_free[k] phase

@@ -229,17 +229,19 @@ bool is_dev(const void* p) {
 // (K-block kb in slot kb & (slots - 1)) where the item's chromosome tiles
 // form one accumulator group, so the MMAs release each K-block as soon as
 // they have used it: 4 slots at 256 patterns (one thread per pattern row
-// fills the K-blocks in order), 8 at 128 patterns (two threads per row; up
-// to 16 K-blocks the second one's range starts within the ring's first
-// pass and the two fill side by side, beyond it waits there for the MMAs
-// of the row's first K-blocks, which still beats narrower tiles on the
-// 256-run workload); else 0 (the width does not fit).
-static_assert(4 * 256 * 128 <= kPhiBudget && 8 * 128 * 128 <= kPhiBudget,
+// fills the K-blocks in order), 8 at 128 and 16 at 64 patterns (two and four
+// threads per row; while the threads' ranges start within the ring's first
+// pass they fill side by side, beyond it a thread waits at its first K-block
+// for the MMAs of the row's earlier ones, which still beats the next
+// narrower tiles); else 0 (the width does not fit).
+static_assert(4 * 256 * 128 <= kPhiBudget && 8 * 128 * 128 <= kPhiBudget &&
+                  16 * 64 * 128 <= kPhiBudget,
               "ring slots exceed the expansion budget");
 int phi_slots(int KB, int C, int bn) {
   if (KB * bn * 128 <= kPhiBudget) return KB;
   if (bn == 256 && C == 1) return 4;
   if (bn == 128 && C <= 2) return 8;
+  if (bn == 64 && C <= 4) return 16;
   return 0;
 }
 

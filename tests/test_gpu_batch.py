@@ -194,9 +194,10 @@ def test_batch_every_degree_matches_cpu_model(tiles):
 # slots (K' from 320 to 2048, templated and generic degrees, ragged tails);
 # two chromosome tiles at 128 patterns, a ring of eight slots filled by two
 # threads per row (beyond 16 K-blocks the second thread's range starts past
-# the ring's first pass); next to runs that use one slot per K-block at 256,
-# 128 and 64 patterns, so that the kernel passes between ring and plain
-# items and between widths.
+# the ring's first pass); three or four at 64 patterns, sixteen slots and four
+# threads per row; next to runs that use one slot per K-block at 256, 128
+# and 64 patterns, so that the kernel passes between ring and plain items
+# and between widths.
 RING_RUNS = [
     (1500, 40, 8, CHEB, 100, 301),     # K' = 320: 5 K-blocks
     (2100, 33, 10, TRIG, 128, 302),    # 660: 11
@@ -211,6 +212,9 @@ RING_RUNS = [
     (900, 64, 8, TRIG, 140, 311),      # 1024, two tiles: 16 K-blocks in 8 slots
     (700, 68, 8, TRIG, 150, 312),      # 1088, two tiles: 17 K-blocks in 8 slots
     (600, 128, 8, TRIG, 200, 313),     # 2048, two tiles: 32 K-blocks in 8 slots
+    (500, 128, 6, TRIG, 300, 314),     # 1536, three tiles: 24 K-blocks in 16 slots at 64
+    (400, 128, 8, TRIG, 450, 315),     # 2048, four tiles: 32 K-blocks in 16 slots
+    (333, 250, 5, CHEB, 390, 316),     # 1250, four tiles: 20 K-blocks in 16 slots
 ]
 
 
@@ -225,7 +229,7 @@ def test_batch_ring_items_match_cpu_model():
         args.append((X, pr.y, d, basis, P, seed))
         probs.append((X, pr.y, d, basis))
     with game.Batch(args, autotune=False) as b:
-        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 128, 128]
+        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 128, 128, 64, 64, 64]
         for gen in range(2):
             if gen:
                 b.generation()

@@ -215,6 +215,8 @@ RING_RUNS = [
     (500, 128, 6, TRIG, 300, 314),     # 1536, three tiles: 24 K-blocks in 16 slots at 64
     (400, 128, 8, TRIG, 450, 315),     # 2048, four tiles: 32 K-blocks in 16 slots
     (333, 250, 5, CHEB, 390, 316),     # 1250, four tiles: 20 K-blocks in 16 slots
+    (1, 128, 8, TRIG, 5, 317),         # 2048, one pattern: a ragged ring tile
+    (129, 100, 7, CHEB, 129, 318),     # 700, two tiles: 128 + 1 patterns, 129 chromosomes
 ]
 
 
@@ -229,7 +231,8 @@ def test_batch_ring_items_match_cpu_model():
         args.append((X, pr.y, d, basis, P, seed))
         probs.append((X, pr.y, d, basis))
     with game.Batch(args, autotune=False) as b:
-        assert b.tiles().tolist() == [256] * 7 + [128, 64, 128, 128, 128, 128, 64, 64, 64]
+        assert b.tiles().tolist() == ([256] * 7 + [128, 64, 128, 128, 128, 128, 64, 64, 64]
+                                      + [256, 128])
         for gen in range(2):
             if gen:
                 b.generation()

@@ -77,30 +77,24 @@ __host__ __device__ inline BSmem bsmem_plan(int phi_bytes, int KBmax) {
 
 // The expansion role's state carried from item to item, and its constants.
 //
-// K-block kb of an item lives in slot kb (ring items: kb mod RK, RK a power
-// of two).
-// Every expansion thread arrives once per K-block on its slot's phi_full
-// barrier (count 256), after its last store into that K-block (at once for a
-// K-block it does not write). Before it stores into, or arrives on, K-block
-// kb of an item it awaits the phi_free phases (the MMAs' release) of every
-// slot <= kb that it arrived on in an earlier item and has not awaited
-// since. A thread's stores and arrivals go in increasing K-block order and
-// the MMA issuer releases K-blocks in increasing order, so this costs no more
-// than awaiting kb alone, and every phase is awaited exactly once, in order,
-// which keeps the parity bits exact. The current item's own arrivals join
-// the pending set only when the item ends: its phi_free phases come after
-// the MMAs of all its chromosome tiles, which need all its K-blocks.
-// Ring items (RK < KB, one accumulator group) reuse slots within the item:
-// there an arrival joins the pending set at once, since the MMAs release a
-// K-block as soon as they have used it, and before its next use (a store or
-// an arrival) the thread awaits that slot alone (other slots' phases may be
-// awaited later, when their own K-blocks come; each slot holds one pending
-// phase at most). With several threads per row, a thread whose range starts
-// past the ring's first pass waits there for the MMAs of the row's earlier
-// K-blocks: slower, never stuck, as every wait is for the MMAs of a lower
-// K-block, whose arrivals come first in each thread's order.
+// K-block kb of an item lives in slot kb; for ring items (RK < KB, one
+// accumulator group) in slot kb & (RK - 1), RK a power of two, so a ring item
+// uses a slot several times. Every expansion thread arrives once per K-block
+// on its slot's phi_full barrier (count 256), after its last store into that
+// K-block (at once for a K-block it does not write), and each arrival leaves
+// the slot pending: before the thread next stores into, or arrives on, that
+// slot it awaits the slot's phi_free phase (the MMAs' release). Each slot
+// thus holds at most one pending phase per thread, every phase is awaited
+// exactly once and in order, and the parity bits stay exact. No thread
+// awaits a release that needs its own later arrivals: a plain item uses each
+// slot once, so its own releases are awaited only by the next item; a ring
+// item has one accumulator group, whose MMAs release a K-block as soon as
+// they have used it. With several threads per row, a thread whose range
+// starts past the ring's first pass waits there for the MMAs of the row's
+// earlier K-blocks: slower, never stuck, as every wait is for the MMAs of a
+// lower K-block, whose arrivals come first in each thread's order.
 struct ExpState {
-  uint32_t pending;    // bit k: arrived on phi_full[k], phi_free phase not yet awaited
+  uint32_t pending;    // bit k: arrived on phi_full[k], its phi_free phase not yet awaited
   uint32_t free_par;   // bit k: parity of the next phi_free[k] phase
   int dead;            // a wait failed (time limit or another role's abort)
 };
@@ -132,47 +126,31 @@ struct RowCursor {
   const ExpEnv& env;
   int BN, r0, colmax;   // colmax = KB * 64
   int rmask;            // K-block kb in slot kb & rmask (all ones unless a ring)
-  bool ring;            // the item reuses slots (RK < KB, RK a power of two)
   int next_arr;         // next K-block to arrive on
-  int awaited;          // the phases K-block `awaited` (and every lower one) needs are awaited
+  int awaited;          // the slot of K-block `awaited` (and of every lower one) is awaited
 
-  // before the first store into, or arrival on, K-block kb
+  // before the first store into, or arrival on, K-block kb: the previous
+  // phase of its slot
   __device__ __forceinline__ void await_for(int kb) {
-    uint32_t m = ring ? 1u << (kb & rmask) : (kb >= 31 ? 0xFFFFFFFFu : ((2u << kb) - 1u));
-    m &= es.pending;
+    const uint32_t m = es.pending & (1u << (kb & rmask));
     if (m != 0u) await_mask(es, env, m);
     awaited = kb;
   }
   __device__ __forceinline__ void arrive(int kb) {
     const int sl = kb & rmask;
     ptx::mbar_arrive(env.phi_full0 + 8u * (uint32_t)sl);
-    if (ring) es.pending |= 1u << sl;
-  }
-  // after the item's last arrival: its K-blocks [0, KB) join the pending set
-  // (ring items: each at its arrival)
-  __device__ __forceinline__ void end_item(int KB) {
-    if (!ring) es.pending |= KB >= 32 ? 0xFFFFFFFFu : ((1u << KB) - 1u);
+    es.pending |= 1u << sl;
   }
   // arrive on K-blocks [next_arr, kbe)
   __device__ __forceinline__ void arrive_below(int kbe) {
     if (kbe <= next_arr || es.dead) return;
-    if (ring) {
-      ptx::fence_proxy_async_smem();
-      for (int k = next_arr; k < kbe; ++k) {
-        if (k > awaited) await_for(k);
-        if (es.dead) return;
-        arrive(k);
-        next_arr = k + 1;
-      }
-      return;
-    }
-    if (kbe - 1 > awaited) {
-      await_for(kbe - 1);
-      if (es.dead) return;
-    }
     ptx::fence_proxy_async_smem();
-    for (int k = next_arr; k < kbe; ++k) arrive(k);
-    next_arr = kbe;
+    for (int k = next_arr; k < kbe; ++k) {
+      if (k > awaited) await_for(k);
+      if (es.dead) return;
+      arrive(k);
+      next_arr = k + 1;
+    }
   }
   __device__ __forceinline__ void store(int col, uint4 val) {
     if (col >= colmax || es.dead) return;
@@ -244,7 +222,7 @@ __device__ __noinline__ ExpState expand_item(ExpState es, const ExpEnv env, cons
   using FG = FeatureGroup<BASIS, D>;
   constexpr int U = FG::U, UF = FG::U * FG::F, UG = FG::U * FG::G;
   constexpr int PD = kRing / UF;   // UF divides 16
-  RowCursor rc{es, env, BN, r0, KB * 64, RK < KB ? RK - 1 : -1, RK < KB, 0, -1};
+  RowCursor rc{es, env, BN, r0, KB * 64, RK < KB ? RK - 1 : -1, 0, -1};
   const int ng = (N + FG::F - 1) / FG::F;
   const int gb = q0 * ng / QS, ge = (q0 + 1) * ng / QS;
   const int cs = gb * FG::G < rc.colmax ? gb * FG::G : rc.colmax;
@@ -278,7 +256,6 @@ __device__ __noinline__ ExpState expand_item(ExpState es, const ExpEnv env, cons
   if (q0 == QS - 1)
     for (int col = ng * FG::G; col < rc.colmax; col += 8) rc.store(col, make_uint4(0, 0, 0, 0));
   rc.arrive_below(KB);
-  rc.end_item(KB);
   return es;
 }
 
@@ -287,7 +264,7 @@ __device__ __noinline__ ExpState expand_item(ExpState es, const ExpEnv env, cons
 __device__ __noinline__ ExpState expand_item_generic(ExpState es, const ExpEnv env,
                                                      const float* xp, const BatchItem R, int r0,
                                                      int q0, int QS) {
-  RowCursor rc{es, env, R.BN, r0, R.KB * 64, R.RK < R.KB ? R.RK - 1 : -1, R.RK < R.KB, 0, -1};
+  RowCursor rc{es, env, R.BN, r0, R.KB * 64, R.RK < R.KB ? R.RK - 1 : -1, 0, -1};
   const int CPT = 8 / QS;
   for (int kb = 0; kb < R.KB && !es.dead; ++kb) {
     for (int qd = q0 * CPT; qd < (q0 + 1) * CPT; ++qd) {
@@ -297,7 +274,6 @@ __device__ __noinline__ ExpState expand_item_generic(ExpState es, const ExpEnv e
     }
     rc.arrive_below(kb + 1);
   }
-  rc.end_item(R.KB);
   return es;
 }
 

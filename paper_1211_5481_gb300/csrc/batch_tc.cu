@@ -152,8 +152,12 @@ struct RowCursor {
       next_arr = k + 1;
     }
   }
+  // es.dead changes only inside a wait, which is checked right after; once
+  // set, the rest of the thread's group still writes its own in-bounds
+  // shared-memory cells and arrives at most once per K-block, and the
+  // caller's loop stops at the next group
   __device__ __forceinline__ void store(int col, uint4 val) {
-    if (col >= colmax || es.dead) return;
+    if (col >= colmax) return;
     const int kb = col >> 6;
     if (kb > awaited) {
       await_for(kb);
